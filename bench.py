@@ -1,0 +1,325 @@
+"""Benchmark: DOF.stages/s of one forward (primal) sweep plus one adjoint sweep
+over a period of the flapping-airfoil workload on one GB300 (or N replicas).
+
+Workload (default "c1"): 2048-triangle seeded O-grid around a 12%-thick
+symmetric airfoil, degree-3 DG (40 DOF/element, 81,920 DOF), 100 DIRK3 steps
+per period, motion = 6 seeded Fourier coefficients.  A step = primal sweep
+(Newton per stage, stored linearization) + adjoint sweep with the QoI terms
+and gradient reconstruction (Eq. uns-disc-adj-dirk2, Eq. funcl-grad-nosens-dirk)
+for F = J_E, the cycle-averaged flapping energy.  Each step starts from the
+previous step's final state (fixed-point iteration toward the periodic orbit).
+
+value = N_u * Nt * 3 stages / (time per step), summed over ranks (replicas).
+Multi-GPU: the path does not shard within one solve; N ranks run N independent
+replicas (scaling "weak", no data-path collective).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF*stages/s fwd+adjoint"
+UNIT = "DOF*stages/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c1")
+    ap.add_argument("--roofline-kernel", default="jacobian")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle sample (CPU)
+def oracle_sample(config, budget_s):
+    """Times the oracle's element-local work of one stage-Newton iteration (residual and
+    exact complex-step Jacobian rows) on as many elements of the workload as fit in
+    budget_s, extrapolated linearly (the element loop is exactly linear) to the mesh.
+    The sparse LU factorization is NOT included, so the oracle's cost is understated."""
+    import numpy as np
+
+    from oracle.dg import DG
+    from pp_inputs import CONFIGS, config_mesh, config_mu, free_stream_state, state_perturbation
+    c = CONFIGS[config]
+    dg = DG(config_mesh(config), c["p"], kin=c["kin"])
+    mu = config_mu(config)
+    u = (free_stream_state(dg.Ne, c["p"]) + state_perturbation(dg.Ne, c["p"], 1, amp=1e-3)).reshape(-1)
+    t0 = time.perf_counter()
+    dg.residual(u, mu, 0.1)
+    t_res = time.perf_counter() - t0
+    done, t_jac, chunk = 0, 0.0, 32
+    while done < dg.Ne and t_jac < budget_s:
+        el = np.arange(done, min(done + chunk, dg.Ne))
+        t0 = time.perf_counter()
+        dg.jac_blocks_subset(u, mu, 0.1, el)
+        t_jac += time.perf_counter() - t0
+        done += len(el)
+    t_jac_full = t_jac * dg.Ne / done
+    # per stage the oracle's Newton evaluates about two Jacobians and a handful of residuals
+    t_stage = 2.0 * t_jac_full + 5.0 * t_res
+    return dict(value=dg.Nu / t_stage, t_res=t_res, t_jac_full=t_jac_full, elems=done, Ne=dg.Ne,
+                seconds=t_res + t_jac, threads=_threads())
+
+
+def _threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return 1
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1512_00616_gb300 import api as A
+    from pp_inputs import CONFIGS, PHYS, config_mesh, config_mu, free_stream_state
+
+    torch.cuda.set_device(local_rank)
+    c = CONFIGS[args.config]
+    mesh = config_mesh(args.config)
+    mu = config_mu(args.config)
+    Nt = c["Nt"]
+    stream = torch.cuda.Stream()
+    cfg = A.pp_config_default(p=c["p"], kin=c["kin"], T=PHYS["T"], device=local_rank, stream=stream.cuda_stream)
+    ctx = A.pp_create(cfg)
+    m = A.pp_mesh_create(ctx, mesh.verts, mesh.tris, mesh.ftag)
+    ne, npn, nu = A.pp_mesh_info(m)
+    dev = f"cuda:{local_rank}"
+    u0 = torch.tensor(free_stream_state(ne, c["p"]).reshape(-1), dtype=torch.float64, device=dev)
+    uN = torch.zeros_like(u0)
+    lamN = torch.zeros_like(u0)
+    lam0 = torch.zeros_like(u0)
+    weights = np.array([-1.0 / PHYS["T"], 0.0])   # F = J_E = -W/T
+    newton = []
+
+    def step():
+        A.pp_primal_period(ctx, m, mu, u0, Nt, u_final=uN)
+        g = A.pp_adjoint_sweep(ctx, lamN, lam0, weights=weights, n_mu=len(mu))
+        u0.copy_(uN)
+        return g
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        A.pp_prof_select(args.roofline_kernel)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local_rank)
+        clk.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = clk.stop()
+        launches_k, kern_ms = A.pp_prof_read()
+        counts = A.pp_prof_counts()
+        ms = ev0.elapsed_time(ev1) / args.steps
+
+        e2e = None
+        if not args.no_e2e:
+            host_u0 = torch.empty(nu, dtype=torch.float64, pin_memory=True)
+            host_u0.copy_(u0.cpu())
+            host_uN = torch.empty_like(host_u0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                u0.copy_(host_u0, non_blocking=True)
+                A.pp_primal_period(ctx, m, mu, u0, Nt, u_final=uN)
+                A.pp_adjoint_sweep(ctx, lamN, lam0, weights=weights, n_mu=len(mu))
+                host_uN.copy_(uN, non_blocking=True)
+                stream.synchronize()
+                host_u0.copy_(host_uN)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms = e0.elapsed_time(e1) / args.steps
+            e2e = dict(ms_per_step=e2e_ms, h2d=nu * 8, d2h=nu * 8 + 8 * len(mu))
+
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    ms = float(tmax.item())
+    A.pp_mesh_destroy(m)
+    A.pp_destroy(ctx)
+    return dict(ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, kern_launches=launches_k, kern_ms=kern_ms,
+                counts=counts, e2e=e2e)
+
+
+def roofline_for(kernel, res, peaks, fp64_tflops, c):
+    """Algorithmic work per launch of the timed kernel class (counts in the design doc)."""
+    p = c["p"]
+    Np = (p + 1) * (p + 2) // 2
+    nb = 4 * Np
+    nqv, nqf = (p + 2) ** 2, p + 2
+    ne = res["ne"]
+    if res["kern_launches"] <= 0:
+        return None
+    t = res["kern_ms"] / res["kern_launches"] * 1e-3
+    if kernel == "jacobian":
+        # contraction: per diagonal entry 2 k x 3 trial terms per volume point + 3 per face point,
+        # per off-diagonal entry 3 per face point (2 flops each)
+        flops = ne * (nb * nb * (2 * nqv * 8 + 3 * nqf * 6) + 3 * nb * nb * nqf * 6)
+        ach = flops / t / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": ach / fp64_tflops if fp64_tflops else None, "traffic": None,
+                "kernel": "k_jacobian", "launches": res["kern_launches"], "avg_us": t * 1e6}
+    if kernel in ("stage_matvec", "block_apply"):
+        blocks = 4 if kernel == "stage_matvec" else 1
+        byts = ne * (blocks * nb * nb * 8 + 2 * nb * 8)
+        ach = byts / t / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "k_" + kernel,
+                "launches": res["kern_launches"], "avg_us": t * 1e6}
+    return None
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from pp_inputs import CONFIGS
+    c = CONFIGS[args.config]
+    workload = (f"{args.config}: {2 * c['n_theta'] * c['n_r']}-triangle O-grid, p={c['p']}, "
+                f"{c['Nt']} DIRK3 steps/period, primal sweep + adjoint sweep (F = J_E, dF/dmu)")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        vals = []
+        budget = max(5.0, 150.0 / max(args.steps + args.warmup, 1))
+        for i in range(args.warmup + args.steps):
+            s = oracle_sample(args.config, budget)
+            if i >= args.warmup:
+                vals.append(s["value"])
+        v = statistics.mean(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["threads"], "kind": "oracle",
+                                 "sample": f"per step: oracle residual + complex-step Jacobian rows on "
+                                           f"{s['elems']}/{s['Ne']} elements (~{budget:.0f} s), extrapolated "
+                                           "linearly to one stage-Newton iteration of the mesh; sparse LU "
+                                           "excluded (oracle cost understated)"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    res = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    from paper_1512_00616_gb300 import api as A
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+    fp64 = A.pp_measure_fp64_peak(local_rank)
+    units = res["nu"] * res["Nt"] * 3
+    value = units / (res["ms"] * 1e-3) * world
+    roof = roofline_for(args.roofline_kernel, res, peaks, fp64, c)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "dof": res["nu"], "elements": res["ne"], "Nt": res["Nt"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set (stored stage Jacobians, ~40 GB) far larger than L2; no flush needed"},
+        "roofline": roof, "fp64_fma_peak_tflops_measured": fp64,
+        "clocks": res["clocks"],
+        "gpu_launches": int(sum(res["counts"].values())),
+        "launches_by_class": res["counts"],
+    }
+    if res["e2e"]:
+        e = res["e2e"]
+        line["e2e"] = {"value": units / (e["ms_per_step"] * 1e-3) * world, "unit": UNIT,
+                       "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
+    if not args.no_cpu_baseline and world == 1:
+        s = oracle_sample(args.config, args.cpu_budget)
+        line["cpu_baseline"] = {"value": s["value"], "unit": UNIT, "cores": s["threads"], "kind": "oracle",
+                                "sample": f"oracle residual + complex-step Jacobian rows on {s['elems']}/{s['Ne']} "
+                                          f"elements ({s['seconds']:.1f} s), extrapolated linearly to one "
+                                          "stage (2 Jacobians + 5 residuals); sparse LU excluded"}
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

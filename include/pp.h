@@ -1,0 +1,186 @@
+/*
+ * pp.h -- C ABI of libpp, a single-GPU (sm_103a) implementation of the fully
+ * discrete periodic shooting and periodic adjoint method of Zahr, Persson and
+ * Wilkening, "A fully discrete adjoint method for optimization of flow problems
+ * on deforming domains with time-periodicity constraints".
+ *
+ * Conventions common to every call
+ * --------------------------------
+ * - Every function returns PP_OK (0) or a negative status code; the message of
+ *   the last failure is available from pp_last_error().  No call aborts, traps
+ *   or exits the process.
+ * - Arrays documented as DEVICE are CUDA device pointers (e.g. torch
+ *   data_ptr()) on the context's device; the caller owns them and the library
+ *   never frees them.  Arrays documented as HOST are ordinary host memory.
+ *   All floating point arrays are IEEE double (FP64).
+ * - State layout ("u layout"): u[(e*4 + a)*Np + i] for element e, conservative
+ *   variable a in (rho, rho*u, rho*v, rho*E) and node i; N_u = Ne*4*Np with
+ *   Np = (p+1)(p+2)/2.  Nodes are equispaced on the reference triangle
+ *   (0,0),(1,0),(0,1), ordered j-major: for j = 0..p, i = 0..p-j, node
+ *   (i/p, j/p); element vertex k maps to the k-th corner.
+ * - Work is issued on the context's stream; calls that return host values
+ *   synchronize that stream before returning.
+ * - Nondimensionalization: chord 1, leading edge at the origin, free stream
+ *   rho = 1, velocity (1, 0), p = 1/(gamma Mach^2), viscosity 1/Re.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PP_OK 0
+#define PP_EINVAL -1      /* invalid argument (sizes, null pointers, bad mesh) */
+#define PP_ENOMEM -2      /* device allocation failed */
+#define PP_ENOCONV -3     /* an iteration hit its cap before its tolerance */
+#define PP_ENAN -4        /* a non-finite value appeared in a norm */
+#define PP_EBREAKDOWN -5  /* Krylov breakdown with a nonzero residual */
+#define PP_ECUDA -6       /* a CUDA runtime call failed */
+#define PP_ESTATE -7      /* call needs a linearization that is not set */
+
+/* motion parametrizations (mu) -- Sec. 6.1 single-Fourier-mode motion */
+#define PP_KIN_HEAVE_PITCH 0 /* mu = (h0, theta0, phi): h = h0 sin(wt), theta = theta0 sin(wt + phi) */
+#define PP_KIN_FOURIER6 1    /* mu = (a1, b1, a2, al1, be1, al2): h = a1 sin wt + b1 cos wt + a2 sin 2wt,
+                                theta = al1 sin wt + be1 cos wt + al2 sin 2wt;  w = 2 pi / T */
+
+typedef struct pp_ctx pp_ctx;
+typedef struct pp_mesh pp_mesh;
+
+typedef struct pp_config {
+  int p;              /* polynomial degree, 1..4 */
+  double gamma;       /* ratio of specific heats (1.4) */
+  double Pr;          /* Prandtl number (0.72) */
+  double Mach;        /* free-stream Mach number (0.2) */
+  double Re;          /* Reynolds number based on chord (1000) */
+  double T;           /* period of the motion (5) */
+  int kin;            /* PP_KIN_* */
+  int device;         /* CUDA device ordinal */
+  void* stream;       /* cudaStream_t to issue work on; NULL = the library's own stream */
+  /* primal stage solves (Newton with GMRES, block-Jacobi preconditioned) */
+  double newton_tol;  /* stop when ||dk||_2 <= newton_tol * max(1, ||u_i||_2) */
+  int newton_maxit;
+  double gmres_rtol;  /* relative tolerance of the Newton-step GMRES */
+  int gmres_restart;
+  int gmres_maxit;    /* cap on GMRES iterations per linear solve */
+  /* tangent and adjoint stage solves (linear, must be tight for exact sensitivities) */
+  double lin_rtol;
+  /* shooting (Algorithm primal) */
+  double nk_gmres_rtol; /* relative tolerance of the shooting GMRES, ||(Phi-I)du - R|| <= rtol ||R|| */
+  int nk_restart;
+  int nk_max_newton;
+  int nk_max_krylov;    /* cap on tangent sweeps per Newton step */
+  /* periodic adjoint (Algorithm dual) */
+  double adj_tol;     /* absolute tolerance on ||lambda^(0)(x) - x||_2 */
+  int adj_restart;
+  int adj_maxit;
+} pp_config;
+
+/* Fills *cfg with the paper's case (Sec. 6.1: gamma 1.4, Pr 0.72, Mach 0.2,
+   Re 1000, T = 5, p = 3) and default tolerances. */
+void pp_config_default(pp_config* cfg);
+
+/* Creates a context on cfg->device.  The context owns all device workspace,
+   including the stored linearization (stage states, element block Jacobians
+   and their block-LU factors, kept in HBM for the whole period).
+   Errors: PP_EINVAL (p out of range, null pointers), PP_ECUDA. */
+int pp_create(const pp_config* cfg, pp_ctx** out);
+int pp_destroy(pp_ctx* ctx);
+const char* pp_last_error(const pp_ctx* ctx);
+const char* pp_version(void);
+
+/* Mesh of straight-sided triangles in the reference configuration (Eq. defmap
+   maps it rigidly to the physical domain).  HOST arrays, copied:
+   verts [nv][2] coordinates; tris [nt][3] counter-clockwise vertex indices;
+   ftag [nt][3] tag of local face f = edge (v_f, v_(f+1)%3): 0 interior,
+   1 wall (no-slip airfoil), 2 far field.
+   Errors: PP_EINVAL if an index is out of range, an element is inverted or a
+   tag contradicts the connectivity (a shared edge must be tagged 0). */
+int pp_mesh_create(pp_ctx* ctx, const double* verts, int nv, const int32_t* tris, const int32_t* ftag,
+                   int nt, pp_mesh** out);
+int pp_mesh_destroy(pp_mesh* mesh);
+/* ne, np (nodes per element) and nu = ne*4*np; any output may be NULL. */
+int pp_mesh_info(const pp_mesh* mesh, int* ne, int* np, int64_t* nu);
+
+/* Semi-discrete residual r(u, mu, t) of M du/dt = r (Eq. semidisc; ALE DG of
+   Sec. 6).  u, r: DEVICE [N_u].  mu: HOST [n_mu]. */
+int pp_residual(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double t, const double* u,
+                double* r);
+
+/* Element block Jacobian dr/du at (u, mu, t): DEVICE blocks [Ne][4][nb][nb]
+   with nb = 4*Np, slot 0 = d r_e / d u_e, slot 1+f = d r_e / d u_(neighbour
+   across face f) (zero for boundary faces).  Each block is stored COLUMN-major:
+   blocks[((e*4 + slot)*nb + col)*nb + row], row/col index (a*Np + i). */
+int pp_jacobian_blocks(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double t,
+                       const double* u, double* blocks);
+
+/* Instantaneous power P^h and x-force F_x^h the fluid exerts on the airfoil
+   (Eq. qoi, instantaneous form).  u: DEVICE; out: HOST [2]. */
+int pp_qoi_rate(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double t, const double* u,
+                double* out);
+
+/* Primal sweep u^(Nt)(u0; mu) over one period (Eq. dirk2) with Nt equal DIRK3
+   steps of dt = T/Nt (T from the config).  u0: DEVICE [N_u].  u_traj: DEVICE
+   [(Nt+1)][N_u] or NULL.  u_final: DEVICE [N_u] or NULL.  qoi: HOST [4] or NULL:
+   (W, J_x, J_E = -W/T, J_T = -J_x/T), W and J_x the solver-consistent
+   discrete work and x-impulse (Eqs. qoi, qoi-disc).
+   The call stores the linearization (stage states, block Jacobians, LU
+   factors) used by pp_tangent_matvec, pp_adjoint_sweep and
+   pp_periodic_adjoint.  Errors: PP_ENOCONV (stage Newton cap), PP_ENAN. */
+int pp_primal_period(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                     double* u_traj, double* u_final, double* qoi);
+
+/* out = (I - du^(Nt)/du0) v about the last primal sweep, by one tangent sweep
+   (Eqs. dirk-sens-mvp and jac-prim-matvec; the sign is that of I - Phi).
+   v, out: DEVICE [N_u] (may alias).  Errors: PP_ESTATE if no sweep is stored. */
+int pp_tangent_matvec(pp_ctx* ctx, const double* v, double* out);
+
+/* Backward adjoint sweep lambda^(0)(lambda_Nt) about the last primal sweep
+   (Eq. uns-disc-adj-dirk2).  weights: HOST [2] weights (w_W, w_x) of
+   F = w_W W + w_x J_x, or NULL for the adjoint sensitivity sweep without QoI
+   terms (Eq. uns-disc-adj-dirk-sens-mvp).  lam_Nt, lam0: DEVICE [N_u] (may
+   alias).  dFdmu: HOST [n_mu] or NULL: with weights, the reconstruction
+   dF/dmu = dF/dmu|explicit + sum_n dt sum_i kappa_i^T dr/dmu
+   (Eq. funcl-grad-nosens-dirk) evaluated with this sweep's multipliers. */
+int pp_adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, double* lam0, double* dFdmu);
+
+typedef struct pp_shoot_stats {
+  int newton_iters;          /* shooting Newton iterations taken */
+  int krylov_iters;          /* tangent sweeps (GMRES matvecs) in total */
+  int primal_sweeps;
+  int stage_newton_iters;    /* summed over all primal stage solves */
+  double residual[64];       /* ||u^(Nt)(u0) - u0||_2 per Newton iterate */
+  double seconds;
+} pp_shoot_stats;
+
+/* Newton-Krylov shooting (Algorithm primal): solves u^(Nt)(u0; mu) = u0 to
+   ||u^(Nt)(u0) - u0||_2 <= tol.  u0_guess: DEVICE [N_u] or NULL (NULL = free
+   stream).  u0_out: DEVICE [N_u] (may alias u0_guess).  qoi: HOST [4] or NULL
+   (as in pp_primal_period, at the returned u0).  On return the stored
+   linearization is that of the returned u0.  stats: HOST or NULL.
+   Errors: PP_ENOCONV (u0_out then holds the last iterate). */
+int pp_shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess, int Nt,
+                double tol, double* u0_out, double* qoi, pp_shoot_stats* stats);
+
+typedef struct pp_adj_stats {
+  int krylov_iters;      /* adjoint sensitivity sweeps in the GMRES */
+  double residual;       /* final ||lambda^(0)(lambda_Nt) - lambda_Nt||_2 */
+  double seconds;
+} pp_adj_stats;
+
+/* Gradient on the manifold of periodic solutions (Algorithms dual and grad).
+   If u0 (DEVICE [N_u]) is non-NULL a primal sweep from u0 first sets the
+   linearization (u0 should be periodic, e.g. from pp_shoot_nk); if NULL the
+   stored linearization is used.  weights: HOST [2] as in pp_adjoint_sweep.
+   F: HOST [1] or NULL; dFdmu: HOST [n_mu]; lam_Nt: DEVICE [N_u] or NULL (the
+   periodic adjoint final condition).  Tolerance adj_tol from the config. */
+int pp_periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                        const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PP_H */

@@ -1,0 +1,42 @@
+/*
+ * pp_prof.h -- diagnostics of libpp used by the benchmark: per-kernel-class
+ * CUDA-event timing on the launching stream, and an FP64 FMA throughput probe.
+ * None of these calls is part of the method; they allocate only CUDA events.
+ */
+#ifndef PP_PROF_H
+#define PP_PROF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* kernel classes */
+#define PP_K_NONE 0
+#define PP_K_JACOBIAN 1      /* element block Jacobian (dual-number quadrature) */
+#define PP_K_RESIDUAL 2      /* residual r(u, mu, t) */
+#define PP_K_STAGE_MATVEC 3  /* alpha M x + beta J x / J^T x over the block-sparse Jacobian */
+#define PP_K_BLOCK_APPLY 4   /* block-Jacobi inverse application (normal / transposed) */
+#define PP_K_BLOCK_INVERSE 5 /* batched Gauss-Jordan inversion of the stage diagonal blocks */
+#define PP_K_KRYLOV 6        /* fused multi-dot / update / norm reductions */
+#define PP_K_OTHER 7         /* vector combinations, QoI and column-sum kernels */
+#define PP_K_COUNT 8
+
+/* Starts timing every launch of kernel class `kind` (one class at a time; PP_K_NONE
+   stops).  Resets the accumulated totals.  Not thread-safe: one host thread drives libpp. */
+int pp_prof_select(int kind);
+/* Synchronizes the device and returns, for the selected class since pp_prof_select,
+   the number of launches and the summed event time in milliseconds. */
+int pp_prof_read(int64_t* launches, double* total_ms);
+/* Counts launches of every class since the last pp_prof_select (no events). */
+int pp_prof_counts(int64_t* counts /* [PP_K_COUNT] */);
+
+/* Measures the device's FP64 FMA throughput (TFLOP/s, 2 flops per FMA) with an
+   unrolled dependent-chain kernel over all SMs; returns PP_OK or PP_ECUDA. */
+int pp_measure_fp64_peak(int device, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -234,6 +234,7 @@ class DG:
                     self.dphiN[e, f] = self.dphi_f[f]
                 self.sigma[e, f] = PENALTY_ETA * self.mu_visc * (p + 1) ** 2 * self.L[e, f] / min(self.area[e], a_nb)
         self.nbr_safe = np.where(self.nbr >= 0, self.nbr, np.arange(Ne)[:, None])
+        self.BinvT_nbr = self.BinvT[self.nbr_safe]                      # [Ne, 3, 2, 2]
 
         # mass matrix: M_e = detB * int phi_i phi_j over the reference triangle
         self.Mref = np.einsum("q,qi,qj->ij", self.w_v, self.phi_v, self.phi_v)
@@ -276,7 +277,8 @@ class DG:
         gm = np.einsum("edk,qik->eqid", P, self.dphi_f[f])
         dUm = np.einsum("...eai,eqid->...eqad", uS, gm)
         Up = np.einsum("...eai,eqi->...eqa", uN[..., f, :, :], self.phiN[:, f])
-        gp = np.einsum("edk,eqik->eqid", P[self.nbr_safe[:, f]], self.dphiN[:, f])
+        Pn = np.einsum("dk,ekl->edl", Q, self.BinvT_nbr[:, f])
+        gp = np.einsum("edk,eqik->eqid", Pn, self.dphiN[:, f])
         dUp = np.einsum("...eai,eqid->...eqad", uN[..., f, :, :], gp)
         n = np.einsum("dk,ek->ed", Q, self.N[:, f])[:, None, :]        # [Ne, 1, 2]
         vG = self.mesh_velocity(self.Xq_f[:, f], Qd, hd)                 # [Ne, nqf, 2]
@@ -324,6 +326,45 @@ class DG:
             H, _ = self._face_flux(uS, uN, f, Q, Qd, hd, P)
             r = r - np.einsum("q,e,qi,...eqa->...eai", self.w_f, self.L[:, f], self.phi_f[f], H)
         return r
+
+    def subset(self, elems):
+        """A view restricted to the rows of the given elements (for sampled checks on
+        large meshes): residual_local on it takes uS = u[elems], uN = u[nbr_safe[elems]]."""
+        import copy
+        sub = copy.copy(self)
+        elems = np.asarray(elems)
+        for name in ("X0", "B", "detB", "area", "BinvT", "L", "N", "Xq_v", "Xq_f", "phiN", "dphiN", "sigma",
+                     "tag", "nbr", "nbr_face", "nbr_safe", "BinvT_nbr"):
+            setattr(sub, name, getattr(self, name)[elems])
+        sub.Ne = len(elems)
+        sub.Nu = sub.Ne * 4 * self.Np
+        return sub
+
+    def jac_blocks_subset(self, u, mu, t, elems):
+        """Block rows of the element Jacobian for the given elements only."""
+        sub = self.subset(elems)
+        nb, Np = self.nb, self.Np
+        us = np.asarray(u, dtype=np.float64).reshape(self.Ne, 4, Np)
+        uS = us[np.asarray(elems)]
+        uN = us[sub.nbr_safe]
+        E = np.eye(nb).reshape(nb, 1, 4, Np)
+        n = sub.Ne
+        out = np.zeros((n, 4, nb, nb))
+        rS = sub.residual_local(uS[None] + 1j * CS_STEP * E, uN[None] + 0j, mu, t)
+        out[:, 0] = np.transpose(np.imag(rS).reshape(nb, n, nb), (1, 2, 0)) / CS_STEP
+        for f in range(3):
+            dN = np.zeros((nb, 1, 3, 4, Np))
+            dN[:, :, f] = E
+            rN = sub.residual_local(uS[None] + 0j, uN[None] + 1j * CS_STEP * dN, mu, t)
+            blk = np.transpose(np.imag(rN).reshape(nb, n, nb), (1, 2, 0)) / CS_STEP
+            blk[sub.nbr[:, f] < 0] = 0.0
+            out[:, 1 + f] = blk
+        return out
+
+    def residual_subset(self, u, mu, t, elems):
+        sub = self.subset(elems)
+        us = np.asarray(u, dtype=np.float64).reshape(self.Ne, 4, self.Np)
+        return sub.residual_local(us[np.asarray(elems)], us[sub.nbr_safe], mu, t)
 
     def gather(self, u):
         u = u.reshape(u.shape[:-1] + (self.Ne, 4, self.Np)) if u.shape[-1] == self.Nu else u

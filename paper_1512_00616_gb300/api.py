@@ -1,0 +1,261 @@
+"""Thin ctypes binding of libpp (include/pp.h): argument marshalling only.
+
+Every function keeps the C name and forwards to libpp; device arrays are
+torch CUDA float64 tensors (their data_ptr() is passed), host arrays are
+numpy float64 arrays.  Nonzero status codes raise PPError with the library's
+message.  There is no fallback: if libpp.so is missing or fails to load,
+importing this module raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpp.so")
+
+PP_OK, PP_EINVAL, PP_ENOMEM, PP_ENOCONV, PP_ENAN, PP_EBREAKDOWN, PP_ECUDA, PP_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+PP_KIN_HEAVE_PITCH, PP_KIN_FOURIER6 = 0, 1
+STATUS_NAMES = {0: "PP_OK", -1: "PP_EINVAL", -2: "PP_ENOMEM", -3: "PP_ENOCONV", -4: "PP_ENAN",
+                -5: "PP_EBREAKDOWN", -6: "PP_ECUDA", -7: "PP_ESTATE"}
+
+EXPORTED = [
+    "pp_version", "pp_config_default", "pp_create", "pp_destroy", "pp_last_error", "pp_mesh_create",
+    "pp_mesh_destroy", "pp_mesh_info", "pp_residual", "pp_jacobian_blocks", "pp_qoi_rate", "pp_primal_period",
+    "pp_tangent_matvec", "pp_adjoint_sweep", "pp_shoot_nk", "pp_periodic_adjoint",
+    # include/pp_prof.h
+    "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak",
+]
+PP_K = dict(none=0, jacobian=1, residual=2, stage_matvec=3, block_apply=4, block_inverse=5, krylov=6, other=7)
+
+
+class pp_config(C.Structure):
+    _fields_ = [("p", C.c_int), ("gamma", C.c_double), ("Pr", C.c_double), ("Mach", C.c_double),
+                ("Re", C.c_double), ("T", C.c_double), ("kin", C.c_int), ("device", C.c_int),
+                ("stream", C.c_void_p), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
+                ("gmres_rtol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
+                ("lin_rtol", C.c_double), ("nk_gmres_rtol", C.c_double), ("nk_restart", C.c_int),
+                ("nk_max_newton", C.c_int), ("nk_max_krylov", C.c_int), ("adj_tol", C.c_double),
+                ("adj_restart", C.c_int), ("adj_maxit", C.c_int)]
+
+
+class pp_shoot_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("krylov_iters", C.c_int), ("primal_sweeps", C.c_int),
+                ("stage_newton_iters", C.c_int), ("residual", C.c_double * 64), ("seconds", C.c_double)]
+
+
+class pp_adj_stats(C.Structure):
+    _fields_ = [("krylov_iters", C.c_int), ("residual", C.c_double), ("seconds", C.c_double)]
+
+
+class PPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpp.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_1512_00616_gb300.build")
+    lib = C.CDLL(LIB_PATH)
+    P, D, I, V = C.c_void_p, C.c_double, C.c_int, None
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "pp_version": (C.c_char_p, []),
+        "pp_config_default": (V, [C.POINTER(pp_config)]),
+        "pp_create": (I, [C.POINTER(pp_config), C.POINTER(P)]),
+        "pp_destroy": (I, [P]),
+        "pp_last_error": (C.c_char_p, [P]),
+        "pp_mesh_create": (I, [P, dp, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), I, C.POINTER(P)]),
+        "pp_mesh_destroy": (I, [P]),
+        "pp_mesh_info": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_int64)]),
+        "pp_residual": (I, [P, P, dp, I, D, P, P]),
+        "pp_jacobian_blocks": (I, [P, P, dp, I, D, P, P]),
+        "pp_qoi_rate": (I, [P, P, dp, I, D, P, dp]),
+        "pp_primal_period": (I, [P, P, dp, I, P, I, P, P, dp]),
+        "pp_tangent_matvec": (I, [P, P, P]),
+        "pp_adjoint_sweep": (I, [P, P, dp, P, dp]),
+        "pp_shoot_nk": (I, [P, P, dp, I, P, I, D, P, dp, C.POINTER(pp_shoot_stats)]),
+        "pp_periodic_adjoint": (I, [P, P, dp, I, P, I, dp, dp, dp, P, C.POINTER(pp_adj_stats)]),
+        "pp_prof_select": (I, [I]),
+        "pp_prof_read": (I, [C.POINTER(C.c_int64), dp]),
+        "pp_prof_counts": (I, [C.POINTER(C.c_int64)]),
+        "pp_measure_fp64_peak": (I, [I, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+# --------------------------------------------------------------------------- helpers
+def _host(a, dtype=np.float64):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double if dtype == np.float64 else C.c_int32))
+
+
+def _dev(t, name):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(ctx, code):
+    if code != PP_OK:
+        msg = _lib.pp_last_error(ctx).decode() if ctx else ""
+        raise PPError(code, msg)
+
+
+# --------------------------------------------------------------------------- entry points
+def pp_version():
+    return _lib.pp_version().decode()
+
+
+def pp_config_default(**overrides):
+    cfg = pp_config()
+    _lib.pp_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def pp_create(cfg=None, **overrides):
+    if cfg is None:
+        cfg = pp_config_default(**overrides)
+    h = C.c_void_p()
+    _check(None, _lib.pp_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def pp_destroy(ctx):
+    _check(None, _lib.pp_destroy(ctx))
+
+
+def pp_last_error(ctx):
+    return _lib.pp_last_error(ctx).decode()
+
+
+def pp_mesh_create(ctx, verts, tris, ftag):
+    v, vp = _host(verts)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    f = np.ascontiguousarray(ftag, dtype=np.int32)
+    h = C.c_void_p()
+    _check(ctx, _lib.pp_mesh_create(ctx, vp, v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    f.ctypes.data_as(C.POINTER(C.c_int32)), t.shape[0], C.byref(h)))
+    return h
+
+
+def pp_mesh_destroy(mesh):
+    _check(None, _lib.pp_mesh_destroy(mesh))
+
+
+def pp_mesh_info(mesh):
+    ne, npn, nu = C.c_int(), C.c_int(), C.c_int64()
+    _check(None, _lib.pp_mesh_info(mesh, C.byref(ne), C.byref(npn), C.byref(nu)))
+    return ne.value, npn.value, nu.value
+
+
+def pp_residual(ctx, mesh, mu, t, u, r):
+    m, mp = _host(mu)
+    _check(ctx, _lib.pp_residual(ctx, mesh, mp, len(m), float(t), _dev(u, "u"), _dev(r, "r")))
+
+
+def pp_jacobian_blocks(ctx, mesh, mu, t, u, blocks):
+    m, mp = _host(mu)
+    _check(ctx, _lib.pp_jacobian_blocks(ctx, mesh, mp, len(m), float(t), _dev(u, "u"), _dev(blocks, "blocks")))
+
+
+def pp_qoi_rate(ctx, mesh, mu, t, u):
+    m, mp = _host(mu)
+    out = np.zeros(2)
+    _check(ctx, _lib.pp_qoi_rate(ctx, mesh, mp, len(m), float(t), _dev(u, "u"), _host(out)[1]))
+    return out
+
+
+def pp_primal_period(ctx, mesh, mu, u0, Nt, u_traj=None, u_final=None):
+    m, mp = _host(mu)
+    qoi = np.zeros(4)
+    _check(ctx, _lib.pp_primal_period(ctx, mesh, mp, len(m), _dev(u0, "u0"), int(Nt), _dev(u_traj, "u_traj"),
+                                      _dev(u_final, "u_final"), qoi.ctypes.data_as(C.POINTER(C.c_double))))
+    return qoi
+
+
+def pp_tangent_matvec(ctx, v, out):
+    _check(ctx, _lib.pp_tangent_matvec(ctx, _dev(v, "v"), _dev(out, "out")))
+
+
+def pp_adjoint_sweep(ctx, lam_Nt, lam0, weights=None, n_mu=0):
+    if weights is not None:
+        w, wp = _host(weights)
+        g = np.zeros(max(n_mu, 1))
+        gp = g.ctypes.data_as(C.POINTER(C.c_double)) if n_mu else None
+    else:
+        wp, g, gp = None, None, None
+    _check(ctx, _lib.pp_adjoint_sweep(ctx, _dev(lam_Nt, "lam_Nt"), wp, _dev(lam0, "lam0"), gp))
+    return g[:n_mu] if (weights is not None and n_mu) else None
+
+
+def pp_shoot_nk(ctx, mesh, mu, Nt, tol, u0_out, u0_guess=None, raise_on_noconv=True):
+    m, mp = _host(mu)
+    qoi = np.zeros(4)
+    st = pp_shoot_stats()
+    code = _lib.pp_shoot_nk(ctx, mesh, mp, len(m), _dev(u0_guess, "u0_guess"), int(Nt), float(tol),
+                            _dev(u0_out, "u0_out"), qoi.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st))
+    if code != PP_ENOCONV or raise_on_noconv:
+        _check(ctx, code)
+    n = min(st.newton_iters + 1, 64)
+    stats = dict(newton_iters=st.newton_iters, krylov_iters=st.krylov_iters, primal_sweeps=st.primal_sweeps,
+                 stage_newton_iters=st.stage_newton_iters, residual=list(st.residual[:n]), seconds=st.seconds,
+                 status=code)
+    return qoi, stats
+
+
+def pp_periodic_adjoint(ctx, mesh, mu, Nt, weights, u0=None, lam_Nt=None):
+    m, mp = _host(mu)
+    w, wp = _host(weights)
+    F = np.zeros(1)
+    g = np.zeros(len(m))
+    st = pp_adj_stats()
+    _check(ctx, _lib.pp_periodic_adjoint(ctx, mesh, mp, len(m), _dev(u0, "u0"), int(Nt), wp,
+                                         F.ctypes.data_as(C.POINTER(C.c_double)),
+                                         g.ctypes.data_as(C.POINTER(C.c_double)), _dev(lam_Nt, "lam_Nt"),
+                                         C.byref(st)))
+    return float(F[0]), g, dict(krylov_iters=st.krylov_iters, residual=st.residual, seconds=st.seconds)
+
+
+# --------------------------------------------------------------------------- diagnostics (include/pp_prof.h)
+def pp_prof_select(kind):
+    k = PP_K[kind] if isinstance(kind, str) else int(kind)
+    _check(None, _lib.pp_prof_select(k))
+
+
+def pp_prof_read():
+    n, ms = C.c_int64(), C.c_double()
+    _check(None, _lib.pp_prof_read(C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+def pp_prof_counts():
+    a = (C.c_int64 * 8)()
+    _check(None, _lib.pp_prof_counts(a))
+    return {k: a[v] for k, v in PP_K.items() if k != "none"}
+
+
+def pp_measure_fp64_peak(device=0):
+    t = C.c_double()
+    _check(None, _lib.pp_measure_fp64_peak(int(device), C.byref(t)))
+    return t.value

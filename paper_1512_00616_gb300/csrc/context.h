@@ -1,0 +1,124 @@
+// Host-side state of libpp: the context (stream, tables, workspace, stored
+// linearization) and the device mesh.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "pp_internal.h"
+
+struct pp_mesh {
+  pp_ctx* ctx = nullptr;
+  int ne = 0;
+  double* d_real = nullptr;  // one allocation for all FP64 geometry arrays
+  int* d_int = nullptr;      // one allocation for nbr, nbrface, tag
+  pp::DevMesh dev{};
+};
+
+namespace pp {
+
+// Reference-element tables computed on the host (see host.cpp).
+struct RefHost {
+  int p = 0, Np = 0, nb = 0, nqv = 0, nqf = 0;
+  std::vector<double> phi_v, dphi_v, w_v, xi_v, phi_f, dphi_f, xi_f, w_f, Mref;
+};
+
+// Krylov workspace of one GMRES level (stage solves and the outer shooting /
+// periodic-adjoint solves each own one, because the latter call the former).
+struct Krylov {
+  int m = 0;
+  int64_t n = 0;
+  double* V = nullptr;   // [m+1][n]
+  double* w = nullptr;   // [n]
+  double* t = nullptr;   // [n]
+  double* r = nullptr;   // [n]
+  double* d_h = nullptr; // [2*(m+1) + 2] device: h1 | h2 | norm2 | y
+  double* h_h = nullptr; // pinned mirror
+  double* d_y = nullptr; // [m+1]
+};
+
+// Motion quantities at one time and their derivatives w.r.t. mu.
+struct Motion {
+  double th, thd, hd;
+  double dth[8], dthd[8], dhd[8];
+};
+
+}  // namespace pp
+
+struct pp_ctx {
+  pp_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  pp::RefHost ref;
+  double* d_tables = nullptr;
+  pp::DevTables tb{};
+  pp::Phys ph{};
+  double A[3][3]{}, b[3]{}, c[3]{};
+
+  // reductions
+  double* d_partial = nullptr;
+  unsigned* d_counter = nullptr;
+  double* d_scalar = nullptr;  // [64]
+  double* h_scalar = nullptr;  // pinned [64]
+  int* d_status = nullptr;
+
+  // per-mesh-size workspace
+  int64_t ws_nu = 0;
+  int ws_ne = 0;
+  double* d_J = nullptr;        // work Jacobian [ne*4*nb*nb]
+  double* d_Ainv = nullptr;     // work inverse [ne*nb*nb]
+  double* d_vec = nullptr;      // pool of work vectors
+  int n_vec = 0;
+  double* d_elem = nullptr;     // [ne*8] per-element partials
+  pp::Krylov kin, kout;         // inner (stage) and outer (shooting / periodic adjoint) GMRES
+
+  // stored linearization (the last primal sweep)
+  const pp_mesh* lin_mesh = nullptr;
+  std::vector<double> lin_mu;
+  int lin_Nt = 0;
+  bool lin_valid = false;
+  size_t store_stages = 0;      // capacity in stages
+  double* st_J = nullptr;       // [stages][ne*4*nb*nb]
+  double* st_Ainv = nullptr;    // [stages][ne*nb*nb]
+  double* st_u = nullptr;       // [stages][nu] stage states
+  std::vector<double> lin_qoi_rates;  // [Nt*3][2]
+  double lin_W = 0.0, lin_Jx = 0.0;
+  int last_newton_iters = 0;
+  int last_gmres_iters = 0;
+};
+
+namespace pp {
+// host.cpp
+int set_error(pp_ctx* ctx, int code, const std::string& msg);
+Motion motion(const pp_ctx* ctx, const double* mu, int n_mu, double t);
+FrameT<double> frame_of(const Motion& mo);
+int check_mu(pp_ctx* ctx, int n_mu);
+int ensure_workspace(pp_ctx* ctx, const pp_mesh* mesh);
+int ensure_store(pp_ctx* ctx, const pp_mesh* mesh, int Nt);
+double* work_vec(pp_ctx* ctx, int i);
+int64_t mesh_nu(const pp_ctx* ctx, const pp_mesh* mesh);
+// solver.cpp
+int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                 double* u_traj, double* u_final, double* qoi);
+int tangent_sweep(pp_ctx* ctx, const double* v, double* out);
+int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, double* lam0, double* dFdmu);
+int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess, int Nt,
+             double tol, double* u0_out, double* qoi, pp_shoot_stats* stats);
+int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                     const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats);
+}  // namespace pp
+
+#define PP_CK(call)                                                                                  \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return pp::set_error(ctx, PP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define PP_TRY(call)        \
+  do {                      \
+    int s_ = (call);        \
+    if (s_ != PP_OK) return s_; \
+  } while (0)

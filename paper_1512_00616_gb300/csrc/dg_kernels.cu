@@ -1,0 +1,481 @@
+// Element-local quadrature kernels of the ALE DG discretization (Sec. 6):
+//  - k_residual     r(u, mu, t) of M du/dt = r (Eq. semidisc); with a dual-valued
+//                   frame it gives dr/ds for a motion seed s (theta, theta', h'),
+//                   the building block of dr/dmu in Eq. funcl-grad-nosens-dirk;
+//  - k_jacobian     element block Jacobian dr/du (diagonal + 3 face-neighbour
+//                   blocks): exact flux derivatives at every quadrature point by
+//                   forward-mode dual numbers, contracted with the basis;
+//  - k_qoi*         instantaneous power and x-force on the wall (Eq. qoi) and
+//                   their exact derivatives with respect to u and the frame.
+//
+// Layouts: u[e][a][i] (nb = 4 Np doubles per element, contiguous); Jacobian
+// blocks [e][slot][col][row] (column-major nb x nb).
+#include "flux.cuh"
+#include "prof.h"
+#include "../../include/pp_prof.h"
+
+namespace pp {
+
+namespace {
+
+constexpr int RES_WARPS = 4;
+constexpr int JAC_THREADS = 128;
+constexpr int NSV = 12;  // volume seeds: U (4) + grad U (8)
+constexpr int NSF = 24;  // face seeds: U-, grad U-, U+, grad U+
+
+template <class T>
+__device__ __forceinline__ void frame_P(const FrameT<T>& fr, const double* BinvT, T P[4]) {
+  // grad_x phi = Q grad_X phi = Q B^{-T} grad_xi phi  =>  P = Q B^{-T}
+  P[0] = fr.Q[0] * BinvT[0] + fr.Q[1] * BinvT[2];
+  P[1] = fr.Q[0] * BinvT[1] + fr.Q[1] * BinvT[3];
+  P[2] = fr.Q[2] * BinvT[0] + fr.Q[3] * BinvT[2];
+  P[3] = fr.Q[2] * BinvT[1] + fr.Q[3] * BinvT[3];
+}
+
+template <class T>
+__device__ __forceinline__ void mesh_velocity(const FrameT<T>& fr, const Phys& ph, double X, double Y, T vG[2]) {
+  double dx = X - ph.x0[0], dy = Y - ph.x0[1];
+  vG[0] = fr.Qd[0] * dx + fr.Qd[1] * dy;
+  vG[1] = fr.Qd[2] * dx + fr.Qd[3] * dy + fr.hd;
+}
+
+__device__ __forceinline__ void ref_to_X(const DevMesh& m, int e, double xi, double eta, double& X, double& Y) {
+  const double* B = m.B + 4 * e;
+  X = m.X0[2 * e] + B[0] * xi + B[1] * eta;
+  Y = m.X0[2 * e + 1] + B[2] * xi + B[3] * eta;
+}
+
+// state and physical gradient at a point from nodal values ue[a*Np + i]
+template <class T>
+__device__ __forceinline__ void interp(const double* ue, int Np, const double* phi, const double* dphi,
+                                       const T P[4], T U[4], T dU[4][2]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    double s = 0.0, s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < Np; ++i) {
+      double c = ue[a * Np + i];
+      s += phi[i] * c;
+      s0 += dphi[2 * i] * c;
+      s1 += dphi[2 * i + 1] * c;
+    }
+    U[a] = T(s);
+    dU[a][0] = P[0] * s0 + P[1] * s1;
+    dU[a][1] = P[2] * s0 + P[3] * s1;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void rotate_normal(const FrameT<T>& fr, const double* N, T n[2]) {
+  n[0] = fr.Q[0] * N[0] + fr.Q[1] * N[1];
+  n[1] = fr.Q[2] * N[0] + fr.Q[3] * N[1];
+}
+
+// ------------------------------------------------------------------------ residual
+template <class T>
+__global__ void __launch_bounds__(RES_WARPS * 32)
+    k_residual(DevMesh m, DevTables tb, Phys ph, FrameT<T> fr, const double* __restrict__ u,
+               double* __restrict__ rval, double* __restrict__ rder) {
+  __shared__ double s_u[RES_WARPS][4 * kMaxNb];
+  __shared__ double s_G[RES_WARPS][kMaxQv * 8 * (sizeof(T) / sizeof(double))];
+  __shared__ double s_H[RES_WARPS][3 * kMaxQf * 4 * (sizeof(T) / sizeof(double))];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * RES_WARPS + warp;
+  if (e >= m.ne) return;
+  const int Np = tb.Np, nb = tb.nb, nqv = tb.nqv, nqf = tb.nqf;
+  double* su = s_u[warp];
+  T* G = reinterpret_cast<T*>(s_G[warp]);
+  T* Hs = reinterpret_cast<T*>(s_H[warp]);
+
+  for (int idx = lane; idx < 4 * nb; idx += 32) {
+    int slot = idx / nb, k = idx - slot * nb;
+    int src = e;
+    if (slot > 0) {
+      int nn = m.nbr[3 * e + slot - 1];
+      src = nn >= 0 ? nn : e;
+    }
+    su[idx] = u[(size_t)src * nb + k];
+  }
+  __syncwarp();
+
+  T P[4];
+  frame_P(fr, m.BinvT + 4 * e, P);
+  const double detB = m.detB[e];
+
+  for (int q = lane; q < nqv; q += 32) {
+    T U[4], dU[4][2], vG[2], F[4][2];
+    interp(su, Np, tb.phi_v + q * Np, tb.dphi_v + 2 * q * Np, P, U, dU);
+    double X, Y;
+    ref_to_X(m, e, tb.xi_v[2 * q], tb.xi_v[2 * q + 1], X, Y);
+    mesh_velocity(fr, ph, X, Y, vG);
+    volume_flux(U, dU, vG, ph, F);
+    double wq = tb.w_v[q] * detB;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      G[(q * 4 + a) * 2 + 0] = wq * (P[0] * F[a][0] + P[2] * F[a][1]);
+      G[(q * 4 + a) * 2 + 1] = wq * (P[1] * F[a][0] + P[3] * F[a][1]);
+    }
+  }
+  for (int idx = lane; idx < 3 * nqf; idx += 32) {
+    int f = idx / nqf, q = idx - f * nqf;
+    T Um[4], dUm[4][2], Up[4], dUp[4][2], n[2], vG[2], H[4];
+    interp(su, Np, tb.phi_f + (f * nqf + q) * Np, tb.dphi_f + 2 * (f * nqf + q) * Np, P, Um, dUm);
+    int tag = m.tag[3 * e + f];
+    if (tag == 0) {
+      int e2 = m.nbr[3 * e + f], g = m.nbrface[3 * e + f], qq = nqf - 1 - q;
+      T P2[4];
+      frame_P(fr, m.BinvT + 4 * e2, P2);
+      interp(su + (1 + f) * nb, Np, tb.phi_f + (g * nqf + qq) * Np, tb.dphi_f + 2 * (g * nqf + qq) * Np, P2, Up,
+             dUp);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        Up[a] = Um[a];
+        dUp[a][0] = dUm[a][0];
+        dUp[a][1] = dUm[a][1];
+      }
+    }
+    rotate_normal(fr, m.N + 6 * e + 2 * f, n);
+    double X, Y;
+    ref_to_X(m, e, tb.xi_f[2 * (f * nqf + q)], tb.xi_f[2 * (f * nqf + q) + 1], X, Y);
+    mesh_velocity(fr, ph, X, Y, vG);
+    face_flux(tag, Um, dUm, Up, dUp, n, vG, m.sigma[3 * e + f], ph, H);
+    double wl = tb.w_f[q] * m.L[3 * e + f];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Hs[(f * kMaxQf + q) * 4 + a] = wl * H[a];
+  }
+  __syncwarp();
+  for (int o = lane; o < nb; o += 32) {
+    int a = o / Np, i = o - a * Np;
+    T acc(0.0);
+    for (int q = 0; q < nqv; ++q) {
+      const double* d = tb.dphi_v + 2 * (q * Np + i);
+      acc += d[0] * G[(q * 4 + a) * 2] + d[1] * G[(q * 4 + a) * 2 + 1];
+    }
+    for (int f = 0; f < 3; ++f)
+      for (int q = 0; q < nqf; ++q) acc -= tb.phi_f[(f * nqf + q) * Np + i] * Hs[(f * kMaxQf + q) * 4 + a];
+    if (rval) rval[(size_t)e * nb + o] = val(acc);
+    if (rder) rder[(size_t)e * nb + o] = der(acc);
+  }
+}
+
+// ------------------------------------------------------------------------ Jacobian
+__global__ void __launch_bounds__(JAC_THREADS)
+    k_jacobian(DevMesh m, DevTables tb, Phys ph, FrameT<double> fr, const double* __restrict__ u,
+               double* __restrict__ J) {
+  __shared__ double su[4 * kMaxNb];
+  __shared__ double Cv[kMaxQv * 4 * 2 * NSV];
+  __shared__ double Cf[3 * kMaxQf * 4 * NSF];
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int Np = tb.Np, nb = tb.nb, nqv = tb.nqv, nqf = tb.nqf;
+  for (int idx = tid; idx < 4 * nb; idx += JAC_THREADS) {
+    int slot = idx / nb, k = idx - slot * nb;
+    int src = e;
+    if (slot > 0) {
+      int nn = m.nbr[3 * e + slot - 1];
+      src = nn >= 0 ? nn : e;
+    }
+    su[idx] = u[(size_t)src * nb + k];
+  }
+  __syncthreads();
+  double P[4];
+  frame_P(fr, m.BinvT + 4 * e, P);
+  const double detB = m.detB[e];
+  FrameT<Dual> frd;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    frd.Q[k] = Dual(fr.Q[k]);
+    frd.Qd[k] = Dual(fr.Qd[k]);
+  }
+  frd.hd = Dual(fr.hd);
+
+  // volume: derivative of the weighted, test-gradient-projected flux per seed
+  for (int task = tid; task < nqv * NSV; task += JAC_THREADS) {
+    int q = task / NSV, s = task - q * NSV;
+    double U0[4], dU0[4][2];
+    interp(su, Np, tb.phi_v + q * Np, tb.dphi_v + 2 * q * Np, P, U0, dU0);
+    Dual U[4], dU[4][2], vG[2], F[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      U[a] = Dual(U0[a], s == a ? 1.0 : 0.0);
+      dU[a][0] = Dual(dU0[a][0], s == 4 + 2 * a ? 1.0 : 0.0);
+      dU[a][1] = Dual(dU0[a][1], s == 5 + 2 * a ? 1.0 : 0.0);
+    }
+    double X, Y;
+    ref_to_X(m, e, tb.xi_v[2 * q], tb.xi_v[2 * q + 1], X, Y);
+    mesh_velocity(frd, ph, X, Y, vG);
+    volume_flux(U, dU, vG, ph, F);
+    double wq = tb.w_v[q] * detB;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Cv[((q * 4 + a) * 2 + 0) * NSV + s] = wq * (P[0] * F[a][0].d + P[2] * F[a][1].d);
+      Cv[((q * 4 + a) * 2 + 1) * NSV + s] = wq * (P[1] * F[a][0].d + P[3] * F[a][1].d);
+    }
+  }
+  // faces
+  for (int task = tid; task < 3 * nqf * NSF; task += JAC_THREADS) {
+    int f = task / (nqf * NSF);
+    int rem = task - f * nqf * NSF;
+    int q = rem / NSF, s = rem - q * NSF;
+    int tag = m.tag[3 * e + f];
+    double* out = Cf + ((f * kMaxQf + q) * 4) * NSF + s;
+    if (tag != 0 && s >= 12) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) out[a * NSF] = 0.0;
+      continue;
+    }
+    double Um0[4], dUm0[4][2], Up0[4], dUp0[4][2];
+    interp(su, Np, tb.phi_f + (f * nqf + q) * Np, tb.dphi_f + 2 * (f * nqf + q) * Np, P, Um0, dUm0);
+    if (tag == 0) {
+      int e2 = m.nbr[3 * e + f], g = m.nbrface[3 * e + f], qq = nqf - 1 - q;
+      double P2[4];
+      frame_P(fr, m.BinvT + 4 * e2, P2);
+      interp(su + (1 + f) * nb, Np, tb.phi_f + (g * nqf + qq) * Np, tb.dphi_f + 2 * (g * nqf + qq) * Np, P2, Up0,
+             dUp0);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        Up0[a] = Um0[a];
+        dUp0[a][0] = dUm0[a][0];
+        dUp0[a][1] = dUm0[a][1];
+      }
+    }
+    Dual Um[4], dUm[4][2], Up[4], dUp[4][2], n[2], vG[2], H[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Um[a] = Dual(Um0[a], s == a ? 1.0 : 0.0);
+      dUm[a][0] = Dual(dUm0[a][0], s == 4 + 2 * a ? 1.0 : 0.0);
+      dUm[a][1] = Dual(dUm0[a][1], s == 5 + 2 * a ? 1.0 : 0.0);
+      Up[a] = Dual(Up0[a], s == 12 + a ? 1.0 : 0.0);
+      dUp[a][0] = Dual(dUp0[a][0], s == 16 + 2 * a ? 1.0 : 0.0);
+      dUp[a][1] = Dual(dUp0[a][1], s == 17 + 2 * a ? 1.0 : 0.0);
+    }
+    rotate_normal(frd, m.N + 6 * e + 2 * f, n);
+    double X, Y;
+    ref_to_X(m, e, tb.xi_f[2 * (f * nqf + q)], tb.xi_f[2 * (f * nqf + q) + 1], X, Y);
+    mesh_velocity(frd, ph, X, Y, vG);
+    face_flux(tag, Um, dUm, Up, dUp, n, vG, m.sigma[3 * e + f], ph, H);
+    double wl = tb.w_f[q] * m.L[3 * e + f];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) out[a * NSF] = wl * H[a].d;
+  }
+  __syncthreads();
+
+  const size_t nb2 = (size_t)nb * nb;
+  double* Jd = J + (size_t)e * 4 * nb2;
+  for (int ent = tid; ent < nb * nb; ent += JAC_THREADS) {
+    int col = ent / nb, row = ent - col * nb;
+    int a = row / Np, i = row - a * Np, b = col / Np, j = col - b * Np;
+    double acc = 0.0;
+    for (int q = 0; q < nqv; ++q) {
+      const double* di = tb.dphi_v + 2 * (q * Np + i);
+      const double* dj = tb.dphi_v + 2 * (q * Np + j);
+      double phij = tb.phi_v[q * Np + j];
+      double g0 = P[0] * dj[0] + P[1] * dj[1];
+      double g1 = P[2] * dj[0] + P[3] * dj[1];
+      const double* C0 = Cv + ((q * 4 + a) * 2) * NSV;
+      const double* C1 = C0 + NSV;
+      double t0 = C0[b] * phij + C0[4 + 2 * b] * g0 + C0[5 + 2 * b] * g1;
+      double t1 = C1[b] * phij + C1[4 + 2 * b] * g0 + C1[5 + 2 * b] * g1;
+      acc += di[0] * t0 + di[1] * t1;
+    }
+    for (int f = 0; f < 3; ++f) {
+      for (int q = 0; q < nqf; ++q) {
+        const double* dj = tb.dphi_f + 2 * ((f * nqf + q) * Np + j);
+        double phii = tb.phi_f[(f * nqf + q) * Np + i];
+        double phij = tb.phi_f[(f * nqf + q) * Np + j];
+        double g0 = P[0] * dj[0] + P[1] * dj[1];
+        double g1 = P[2] * dj[0] + P[3] * dj[1];
+        const double* C = Cf + ((f * kMaxQf + q) * 4 + a) * NSF;
+        acc -= phii * (C[b] * phij + C[4 + 2 * b] * g0 + C[5 + 2 * b] * g1);
+      }
+    }
+    Jd[(size_t)col * nb + row] = acc;
+  }
+  for (int f = 0; f < 3; ++f) {
+    double* Jf = Jd + (size_t)(1 + f) * nb2;
+    int tag = m.tag[3 * e + f];
+    if (tag != 0) {
+      for (int ent = tid; ent < nb * nb; ent += JAC_THREADS) Jf[ent] = 0.0;
+      continue;
+    }
+    int e2 = m.nbr[3 * e + f], g = m.nbrface[3 * e + f];
+    double P2[4];
+    frame_P(fr, m.BinvT + 4 * e2, P2);
+    for (int ent = tid; ent < nb * nb; ent += JAC_THREADS) {
+      int col = ent / nb, row = ent - col * nb;
+      int a = row / Np, i = row - a * Np, b = col / Np, j = col - b * Np;
+      double acc = 0.0;
+      for (int q = 0; q < nqf; ++q) {
+        int qq = nqf - 1 - q;
+        const double* dj = tb.dphi_f + 2 * ((g * nqf + qq) * Np + j);
+        double phii = tb.phi_f[(f * nqf + q) * Np + i];
+        double phij = tb.phi_f[(g * nqf + qq) * Np + j];
+        double g0 = P2[0] * dj[0] + P2[1] * dj[1];
+        double g1 = P2[2] * dj[0] + P2[3] * dj[1];
+        const double* C = Cf + ((f * kMaxQf + q) * 4 + a) * NSF;
+        acc -= phii * (C[12 + b] * phij + C[16 + 2 * b] * g0 + C[17 + 2 * b] * g1);
+      }
+      Jf[(size_t)col * nb + row] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ QoI
+// Per element: sum over its wall faces of w L (f . v_G, f_x), f = momentum part of the wall flux.
+template <class T>
+__global__ void __launch_bounds__(RES_WARPS * 32)
+    k_qoi(DevMesh m, DevTables tb, Phys ph, FrameT<T> fr, const double* __restrict__ u, double* __restrict__ out,
+          int want_der) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * RES_WARPS + warp;
+  if (e >= m.ne) return;
+  const int Np = tb.Np, nb = tb.nb, nqf = tb.nqf;
+  const double* ue = u + (size_t)e * nb;
+  T P[4];
+  frame_P(fr, m.BinvT + 4 * e, P);
+  T pw(0.0), fx(0.0);
+  for (int idx = lane; idx < 3 * nqf; idx += 32) {
+    int f = idx / nqf, q = idx - f * nqf;
+    if (m.tag[3 * e + f] != 1) continue;
+    T Um[4], dUm[4][2], n[2], vG[2], H[4];
+    interp(ue, Np, tb.phi_f + (f * nqf + q) * Np, tb.dphi_f + 2 * (f * nqf + q) * Np, P, Um, dUm);
+    rotate_normal(fr, m.N + 6 * e + 2 * f, n);
+    double X, Y;
+    ref_to_X(m, e, tb.xi_f[2 * (f * nqf + q)], tb.xi_f[2 * (f * nqf + q) + 1], X, Y);
+    mesh_velocity(fr, ph, X, Y, vG);
+    face_flux(1, Um, dUm, Um, dUm, n, vG, m.sigma[3 * e + f], ph, H);
+    double wl = tb.w_f[q] * m.L[3 * e + f];
+    pw += wl * (H[1] * vG[0] + H[2] * vG[1]);
+    fx += wl * H[1];
+  }
+  double a0 = want_der ? der(pw) : val(pw);
+  double a1 = want_der ? der(fx) : val(fx);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+  }
+  if (lane == 0) {
+    out[2 * e] = a0;
+    out[2 * e + 1] = a1;
+  }
+}
+
+// g_e = d(w0 P^h + w1 F_x^h)/du_e on wall elements (zero elsewhere)
+__global__ void __launch_bounds__(RES_WARPS * 32)
+    k_qoi_du(DevMesh m, DevTables tb, Phys ph, FrameT<double> fr, const double* __restrict__ u, double w0, double w1,
+             double* __restrict__ g) {
+  __shared__ double s_C[RES_WARPS][3 * kMaxQf * NSV];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * RES_WARPS + warp;
+  if (e >= m.ne) return;
+  const int Np = tb.Np, nb = tb.nb, nqf = tb.nqf;
+  const bool wall = m.tag[3 * e] == 1 || m.tag[3 * e + 1] == 1 || m.tag[3 * e + 2] == 1;
+  if (!wall) {
+    for (int o = lane; o < nb; o += 32) g[(size_t)e * nb + o] = 0.0;
+    return;
+  }
+  double* C = s_C[warp];
+  const double* ue = u + (size_t)e * nb;
+  double P[4];
+  frame_P(fr, m.BinvT + 4 * e, P);
+  FrameT<Dual> frd;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    frd.Q[k] = Dual(fr.Q[k]);
+    frd.Qd[k] = Dual(fr.Qd[k]);
+  }
+  frd.hd = Dual(fr.hd);
+  for (int task = lane; task < 3 * nqf * NSV; task += 32) {
+    int f = task / (nqf * NSV);
+    int rem = task - f * nqf * NSV;
+    int q = rem / NSV, s = rem - q * NSV;
+    if (m.tag[3 * e + f] != 1) {
+      C[(f * kMaxQf + q) * NSV + s] = 0.0;
+      continue;
+    }
+    double U0[4], dU0[4][2];
+    interp(ue, Np, tb.phi_f + (f * nqf + q) * Np, tb.dphi_f + 2 * (f * nqf + q) * Np, P, U0, dU0);
+    Dual Um[4], dUm[4][2], n[2], vG[2], H[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Um[a] = Dual(U0[a], s == a ? 1.0 : 0.0);
+      dUm[a][0] = Dual(dU0[a][0], s == 4 + 2 * a ? 1.0 : 0.0);
+      dUm[a][1] = Dual(dU0[a][1], s == 5 + 2 * a ? 1.0 : 0.0);
+    }
+    rotate_normal(frd, m.N + 6 * e + 2 * f, n);
+    double X, Y;
+    ref_to_X(m, e, tb.xi_f[2 * (f * nqf + q)], tb.xi_f[2 * (f * nqf + q) + 1], X, Y);
+    mesh_velocity(frd, ph, X, Y, vG);
+    face_flux(1, Um, dUm, Um, dUm, n, vG, m.sigma[3 * e + f], ph, H);
+    double wl = tb.w_f[q] * m.L[3 * e + f];
+    Dual val = w0 * (H[1] * vG[0] + H[2] * vG[1]) + w1 * H[1];
+    C[(f * kMaxQf + q) * NSV + s] = wl * val.d;
+  }
+  __syncwarp();
+  for (int o = lane; o < nb; o += 32) {
+    int b = o / Np, j = o - b * Np;
+    double acc = 0.0;
+    for (int f = 0; f < 3; ++f) {
+      if (m.tag[3 * e + f] != 1) continue;
+      for (int q = 0; q < nqf; ++q) {
+        const double* dj = tb.dphi_f + 2 * ((f * nqf + q) * Np + j);
+        double phij = tb.phi_f[(f * nqf + q) * Np + j];
+        double g0 = P[0] * dj[0] + P[1] * dj[1];
+        double g1 = P[2] * dj[0] + P[3] * dj[1];
+        const double* Cq = C + (f * kMaxQf + q) * NSV;
+        acc += Cq[b] * phij + Cq[4 + 2 * b] * g0 + Cq[5 + 2 * b] * g1;
+      }
+    }
+    g[(size_t)e * nb + o] = acc;
+  }
+}
+
+}  // namespace
+
+static int res_blocks(int ne) { return (ne + RES_WARPS - 1) / RES_WARPS; }
+
+cudaError_t launch_residual(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                            const double* u, double* r, cudaStream_t st) {
+  ProfScope ps(PP_K_RESIDUAL, st);
+  k_residual<double><<<res_blocks(m.ne), RES_WARPS * 32, 0, st>>>(m, tb, ph, fr, u, r, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_dframe(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<Dual>& fr,
+                                   const double* u, double* dr, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_residual<Dual><<<res_blocks(m.ne), RES_WARPS * 32, 0, st>>>(m, tb, ph, fr, u, nullptr, dr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                            const double* u, double* J, cudaStream_t st) {
+  ProfScope ps(PP_K_JACOBIAN, st);
+  k_jacobian<<<m.ne, JAC_THREADS, 0, st>>>(m, tb, ph, fr, u, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qoi(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                       const double* u, double* per_elem, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_qoi<double><<<res_blocks(m.ne), RES_WARPS * 32, 0, st>>>(m, tb, ph, fr, u, per_elem, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qoi_dframe(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<Dual>& fr,
+                              const double* u, double* per_elem, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_qoi<Dual><<<res_blocks(m.ne), RES_WARPS * 32, 0, st>>>(m, tb, ph, fr, u, per_elem, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qoi_du(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                          const double* u, double w0, double w1, double* g, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_qoi_du<<<res_blocks(m.ne), RES_WARPS * 32, 0, st>>>(m, tb, ph, fr, u, w0, w1, g);
+  return cudaGetLastError();
+}
+
+}  // namespace pp

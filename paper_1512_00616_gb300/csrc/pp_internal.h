@@ -1,0 +1,162 @@
+// Internal declarations of libpp: device-side views of the mesh and the
+// reference tables, the forward-mode dual number used for exact derivatives,
+// and the kernel launch wrappers shared by the host-side solvers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pp.h"
+
+#define PP_HD __host__ __device__ __forceinline__
+
+namespace pp {
+
+constexpr int kMaxP = 4;
+constexpr int kMaxNp = 15;   // (p+1)(p+2)/2 at p = 4
+constexpr int kMaxNb = 60;   // 4 * kMaxNp
+constexpr int kMaxQv = 36;   // (p+2)^2 volume points at p = 4
+constexpr int kMaxQf = 6;    // p+2 face points at p = 4
+constexpr int kStages = 3;
+
+// ---------------------------------------------------------------- dual numbers
+// Forward-mode derivative carrier: value v and one directional derivative d.
+struct Dual {
+  double v, d;
+  PP_HD Dual() : v(0.0), d(0.0) {}
+  PP_HD Dual(double a) : v(a), d(0.0) {}
+  PP_HD Dual(double a, double b) : v(a), d(b) {}
+};
+PP_HD Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+PP_HD Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+PP_HD Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+PP_HD Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+PP_HD Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+PP_HD Dual operator+(Dual a, double b) { return Dual(a.v + b, a.d); }
+PP_HD Dual operator+(double a, Dual b) { return Dual(a + b.v, b.d); }
+PP_HD Dual operator-(Dual a, double b) { return Dual(a.v - b, a.d); }
+PP_HD Dual operator-(double a, Dual b) { return Dual(a - b.v, -b.d); }
+PP_HD Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+PP_HD Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
+PP_HD Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
+PP_HD Dual operator/(double a, Dual b) {
+  double q = a / b.v;
+  return Dual(q, -q * b.d / b.v);
+}
+PP_HD Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+PP_HD Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+PP_HD Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
+
+PP_HD double val(double a) { return a; }
+PP_HD double val(Dual a) { return a.v; }
+PP_HD double der(double) { return 0.0; }
+PP_HD double der(Dual a) { return a.d; }
+__device__ __forceinline__ double sqrtT(double a) { return sqrt(a); }
+__device__ __forceinline__ Dual sqrtT(Dual a) {
+  double s = sqrt(a.v);
+  return Dual(s, 0.5 * a.d / s);
+}
+// |a| with the branch taken on the value (exact derivative away from a = 0)
+PP_HD double absT(double a) { return a >= 0.0 ? a : -a; }
+PP_HD Dual absT(Dual a) { return a.v >= 0.0 ? a : -a; }
+
+// ---------------------------------------------------------------- physics and motion
+struct Phys {
+  double gam, Pr, mu;   // mu: dynamic viscosity 1/Re
+  double Uinf[4];
+  double x0[2];         // pitching axis in the reference configuration
+};
+
+// Rigid-body frame of Eq. defmap at one time: Q (row-major), Q' and h'.
+template <class T>
+struct FrameT {
+  T Q[4];
+  T Qd[4];
+  T hd;
+};
+
+// ---------------------------------------------------------------- device views
+struct DevTables {
+  int p, Np, nb, nqv, nqf;
+  const double* phi_v;   // [nqv][Np]
+  const double* dphi_v;  // [nqv][Np][2]  d/dxi, d/deta
+  const double* w_v;     // [nqv], sum 1/2
+  const double* xi_v;    // [nqv][2]
+  const double* phi_f;   // [3][nqf][Np]
+  const double* dphi_f;  // [3][nqf][Np][2]
+  const double* xi_f;    // [3][nqf][2]
+  const double* w_f;     // [nqf], sum 1
+  const double* Mref;    // [Np][Np]
+};
+
+struct DevMesh {
+  int ne;
+  const double* X0;      // [ne][2]
+  const double* B;       // [ne][4]  row-major 2x2, columns = edge vectors
+  const double* BinvT;   // [ne][4]  row-major
+  const double* detB;    // [ne]
+  const double* N;       // [ne][3][2] reference outward unit normals
+  const double* L;       // [ne][3]   face lengths
+  const double* sigma;   // [ne][3]   interior-penalty coefficients
+  const int* nbr;        // [ne][3]   neighbour or -1
+  const int* nbrface;    // [ne][3]
+  const int* tag;        // [ne][3]   0 interior, 1 wall, 2 far field
+};
+
+// ---------------------------------------------------------------- kernel wrappers
+// All take the stream explicitly and return the launch error (cudaSuccess on success).
+cudaError_t launch_residual(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                            const double* u, double* r, cudaStream_t st);
+// derivative of r with respect to a frame seed (the frame carries the derivative)
+cudaError_t launch_residual_dframe(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<Dual>& fr,
+                                   const double* u, double* dr, cudaStream_t st);
+cudaError_t launch_jacobian(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                            const double* u, double* J, cudaStream_t st);
+// per-element (P^h, F_x^h) contributions [ne][2]
+cudaError_t launch_qoi(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                       const double* u, double* per_elem, cudaStream_t st);
+cudaError_t launch_qoi_dframe(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<Dual>& fr,
+                              const double* u, double* per_elem, cudaStream_t st);
+// g = d(w0 P^h + w1 F_x^h)/du  (DEVICE [N_u], zero away from the wall)
+cudaError_t launch_qoi_du(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
+                          const double* u, double w0, double w1, double* g, cudaStream_t st);
+
+// Stage matrix A_e = detB_e Mref (x) I4 - c J_ee, inverted per element (Gauss-Jordan, partial pivoting).
+cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const double* J, double c, double* Ainv,
+                                 int* status, cudaStream_t st);
+// y = alpha M x + beta J x  (trans = 0)  or  alpha M x + beta J^T x  (trans = 1); J may be null if beta == 0
+cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const double* J, double alpha, double beta,
+                                const double* x, double* y, int trans, cudaStream_t st);
+// y = Ainv x (trans = 0) or Ainv^T x (trans = 1), per element
+cudaError_t launch_block_apply(const DevMesh& m, int nb, const double* Ainv, const double* x, double* y, int trans,
+                               cudaStream_t st);
+
+// vectors of length n
+cudaError_t launch_lincomb(int64_t n, double* y, int nterms, const double* c, const double* const* x,
+                           cudaStream_t st);  // y = sum c_k x_k (y may alias one x_k)
+cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaStream_t st);  // y = a x
+// out[j] = V_j . w for j < k, V contiguous with stride ldv; deterministic two-level reduction
+cudaError_t launch_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* w, double* out,
+                        double* partial, unsigned* counter, cudaStream_t st);
+// w -= V h[0:k]; then out[0:k] = V_j . w  (fused CGS second pass)
+cudaError_t launch_update_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
+                               double* out, double* partial, unsigned* counter, cudaStream_t st);
+// w -= V h[0:k]; then out[0] = w . w
+cudaError_t launch_update_norm2(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
+                                double* out, double* partial, unsigned* counter, cudaStream_t st);
+// out[0] = x . y
+cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out, double* partial,
+                       unsigned* counter, cudaStream_t st);
+// out[j] = sum over elements of per_elem[e][j], j < k (k <= 8)
+cudaError_t launch_colsum(int ne, int k, const double* per_elem, double* out, double* partial, unsigned* counter,
+                          cudaStream_t st);
+
+int reduction_blocks();  // number of partial sums used by the reductions
+
+}  // namespace pp

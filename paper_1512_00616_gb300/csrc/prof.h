@@ -1,0 +1,15 @@
+// Hooks used by the launch wrappers to time one kernel class (include/pp_prof.h).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pp {
+void prof_begin(int kind, cudaStream_t st, cudaEvent_t* stop_out);
+void prof_end(cudaEvent_t stop, cudaStream_t st);
+
+struct ProfScope {
+  cudaEvent_t stop;
+  cudaStream_t st;
+  ProfScope(int kind, cudaStream_t s) : st(s) { prof_begin(kind, s, &stop); }
+  ~ProfScope() { prof_end(stop, st); }
+};
+}  // namespace pp

@@ -1,0 +1,559 @@
+// Host-driven solvers of libpp; every vector lives in device memory and every
+// arithmetic step runs in the kernels of dg_kernels.cu / linalg_kernels.cu.
+// Only Krylov scalars (Hessenberg column, norms) cross to the host.
+//
+//  - gmres():          restarted, right-preconditioned GMRES with classical
+//                      Gram-Schmidt applied twice (fused update + multi-dot
+//                      kernels), Givens rotations on the host.  Used for the
+//                      stage solves (block-Jacobi preconditioned) and, without
+//                      preconditioner, for the shooting system (Algorithm primal)
+//                      and the periodic adjoint system (Algorithm dual).
+//  - primal_sweep():   Eq. dirk2: DIRK3 steps, Newton per stage on
+//                      R_i = M k_i - dt r(u_i); stores u_i, dr/du(u_i) and the
+//                      block-Jacobi inverse at the converged stage.
+//  - tangent_sweep():  Eq. dirk-sens-mvp, returns v - Phi v.
+//  - adjoint_sweep():  Eq. uns-disc-adj-dirk2 (with QoI terms) or
+//                      Eq. uns-disc-adj-dirk-sens-mvp (without), plus the
+//                      gradient reconstruction of Eq. funcl-grad-nosens-dirk.
+//  - shoot_nk(), periodic_adjoint(): Algorithms primal, dual and grad.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+
+#include "context.h"
+
+namespace pp {
+
+namespace {
+
+using Op = std::function<int(const double* x, double* y)>;
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int host_dot(pp_ctx* ctx, int64_t n, const double* x, const double* y, double* out) {
+  PP_CK(launch_dot(n, x, y, ctx->d_scalar, ctx->d_partial, ctx->d_counter, ctx->stream));
+  PP_CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  *out = ctx->h_scalar[0];
+  return PP_OK;
+}
+
+int host_norm(pp_ctx* ctx, int64_t n, const double* x, double* out) {
+  double d;
+  PP_TRY(host_dot(ctx, n, x, x, &d));
+  *out = std::sqrt(d);
+  if (!std::isfinite(*out)) return set_error(ctx, PP_ENAN, "non-finite norm");
+  return PP_OK;
+}
+
+int lincomb(pp_ctx* ctx, int64_t n, double* y, std::initializer_list<double> c, std::initializer_list<const double*> x) {
+  double cc[4];
+  const double* xx[4];
+  int k = 0;
+  auto it = x.begin();
+  for (double v : c) {
+    cc[k] = v;
+    xx[k] = *it++;
+    ++k;
+  }
+  PP_CK(launch_lincomb(n, y, k, cc, xx, ctx->stream));
+  return PP_OK;
+}
+
+int copy(pp_ctx* ctx, int64_t n, double* y, const double* x) {
+  if (y != x) PP_CK(cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  return PP_OK;
+}
+
+// Right-preconditioned restarted GMRES for A x = b, x0 = 0.  Stops when
+// ||b - A x|| <= max(rtol ||b||, atol) (Arnoldi estimate) or after maxit
+// Krylov steps.  prec may be empty (no preconditioner).
+int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, double* x, double rtol, double atol,
+          int maxit, int* iters, double* res_out) {
+  const int64_t n = K.n;
+  const int m = K.m;
+  double bnorm;
+  PP_TRY(host_norm(ctx, n, b, &bnorm));
+  PP_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+  if (iters) *iters = 0;
+  if (res_out) *res_out = bnorm;
+  if (bnorm == 0.0) return PP_OK;
+  const double tol = std::fmax(rtol * bnorm, atol);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  int total = 0;
+  double beta = bnorm;
+  PP_TRY(copy(ctx, n, K.r, b));
+  bool done = false;
+  while (!done) {
+    PP_CK(launch_scale(n, K.V, 1.0 / beta, K.r, ctx->stream));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    double res = beta;
+    for (; j < m; ++j) {
+      double* vj = K.V + (size_t)j * n;
+      const double* z = vj;
+      if (prec) {
+        PP_TRY(prec(vj, K.t));
+        z = K.t;
+      }
+      PP_TRY(A(z, K.w));
+      double* d_h1 = K.d_h;
+      double* d_h2 = K.d_h + (m + 2);
+      double* d_nrm = K.d_h + 2 * (m + 2);
+      PP_CK(launch_mdot(n, K.V, n, j + 1, K.w, d_h1, ctx->d_partial, ctx->d_counter, ctx->stream));
+      PP_CK(launch_update_mdot(n, K.V, n, j + 1, d_h1, K.w, d_h2, ctx->d_partial, ctx->d_counter, ctx->stream));
+      PP_CK(launch_update_norm2(n, K.V, n, j + 1, d_h2, K.w, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
+      PP_CK(cudaMemcpyAsync(K.h_h, K.d_h, sizeof(double) * (2 * (m + 2) + 1), cudaMemcpyDeviceToHost, ctx->stream));
+      PP_CK(cudaStreamSynchronize(ctx->stream));
+      double* col = &H[(size_t)j * (m + 1)];
+      for (int i = 0; i <= j; ++i) col[i] = K.h_h[i] + K.h_h[(m + 2) + i];
+      double hn = std::sqrt(std::fmax(K.h_h[2 * (m + 2)], 0.0));
+      if (!std::isfinite(hn)) return set_error(ctx, PP_ENAN, "GMRES: non-finite Arnoldi norm");
+      col[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      double rr = std::hypot(col[j], col[j + 1]);
+      cs[j] = rr > 0 ? col[j] / rr : 1.0;
+      sn[j] = rr > 0 ? col[j + 1] / rr : 0.0;
+      col[j] = rr;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      res = std::fabs(g[j + 1]);
+      ++total;
+      bool stop = res <= tol || total >= maxit || hn == 0.0;
+      if (!stop) PP_CK(launch_scale(n, K.V + (size_t)(j + 1) * n, 1.0 / hn, K.w, ctx->stream));
+      if (stop) {
+        ++j;
+        break;
+      }
+    }
+    if (j > m) j = m;
+    // back substitution H y = g on the j x j upper triangle
+    for (int i = j - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < j; ++k) s -= H[(size_t)k * (m + 1) + i] * y[k];
+      y[i] = s / H[(size_t)i * (m + 1) + i];
+    }
+    // x += P^{-1} V y: t = V y via the fused update kernel (w := 0 - V(-y))
+    for (int i = 0; i < j; ++i) K.h_h[i] = -y[i];
+    PP_CK(cudaMemcpyAsync(K.d_y, K.h_h, sizeof(double) * j, cudaMemcpyHostToDevice, ctx->stream));
+    PP_CK(cudaMemsetAsync(K.w, 0, sizeof(double) * n, ctx->stream));
+    PP_CK(launch_update_norm2(n, K.V, n, j, K.d_y, K.w, ctx->d_scalar, ctx->d_partial, ctx->d_counter, ctx->stream));
+    if (prec) {
+      PP_TRY(prec(K.w, K.t));
+      PP_TRY(lincomb(ctx, n, x, {1.0, 1.0}, {x, K.t}));
+    } else {
+      PP_TRY(lincomb(ctx, n, x, {1.0, 1.0}, {x, K.w}));
+    }
+    if (res <= tol || total >= maxit) {
+      done = true;
+      break;
+    }
+    // restart from the true residual r = b - A x
+    const double* z = x;
+    if (prec) {
+      // x is already the preconditioned solution; A acts on it directly
+    }
+    PP_TRY(A(z, K.w));
+    PP_TRY(lincomb(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
+    PP_TRY(host_norm(ctx, n, K.r, &beta));
+    if (beta <= tol) break;
+  }
+  // the last synchronous copy above leaves the stream in order; report
+  if (iters) *iters = total;
+  if (res_out) *res_out = 0.0;
+  return total >= maxit ? PP_ENOCONV : PP_OK;
+}
+
+struct StageView {
+  const double* J;
+  const double* Ainv;
+  double c;  // a_ii dt
+};
+
+int stage_solve(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans, const double* b, double* x,
+                double rtol, double atol, int* iters) {
+  const DevMesh& m = mesh->dev;
+  Op A = [&](const double* in, double* out) {
+    PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 1.0, -sv.c, in, out, trans, ctx->stream));
+    return PP_OK;
+  };
+  Op P = [&](const double* in, double* out) {
+    PP_CK(launch_block_apply(m, ctx->tb.nb, sv.Ainv, in, out, trans, ctx->stream));
+    return PP_OK;
+  };
+  int st = gmres(ctx, ctx->kin, A, P, b, x, rtol, atol, ctx->cfg.gmres_maxit, iters, nullptr);
+  if (st == PP_ENOCONV) return set_error(ctx, PP_ENOCONV, "stage GMRES hit gmres_maxit");
+  return st;
+}
+
+size_t nb2(const pp_ctx* ctx) { return (size_t)ctx->tb.nb * ctx->tb.nb; }
+
+StageView stored_stage(pp_ctx* ctx, int n, int i) {
+  size_t s = (size_t)n * 3 + i;
+  size_t ne = ctx->lin_mesh->ne;
+  return StageView{ctx->st_J + s * ne * 4 * nb2(ctx), ctx->st_Ainv + s * ne * nb2(ctx),
+                   ctx->A[i][i] * ctx->cfg.T / ctx->lin_Nt};
+}
+
+const double* stored_u(pp_ctx* ctx, int n, int i) {
+  return ctx->st_u + ((size_t)n * 3 + i) * ctx->ws_nu;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------- primal sweep
+int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                 double* u_traj, double* u_final, double* qoi) {
+  PP_TRY(ensure_store(ctx, mesh, Nt));
+  ctx->lin_valid = false;
+  ctx->lin_mesh = mesh;
+  ctx->lin_mu.assign(mu, mu + n_mu);
+  ctx->lin_Nt = Nt;
+  const DevMesh& m = mesh->dev;
+  const int64_t n = ctx->ws_nu;
+  const double dt = ctx->cfg.T / Nt;
+  double* u = work_vec(ctx, 0);
+  double* k[3] = {work_vec(ctx, 1), work_vec(ctx, 2), work_vec(ctx, 3)};
+  double* base = work_vec(ctx, 4);
+  double* r = work_vec(ctx, 5);
+  double* R = work_vec(ctx, 6);
+  double* dk = work_vec(ctx, 7);
+  double* kprev = work_vec(ctx, 8);
+  PP_TRY(copy(ctx, n, u, u0));
+  PP_CK(cudaMemsetAsync(kprev, 0, sizeof(double) * n, ctx->stream));
+  if (u_traj) PP_TRY(copy(ctx, n, u_traj, u));
+  ctx->lin_qoi_rates.assign((size_t)Nt * 6, 0.0);
+  double* d_rates = ctx->d_elem;  // reused below through colsum -> d_scalar
+  (void)d_rates;
+  ctx->last_newton_iters = 0;
+  ctx->last_gmres_iters = 0;
+  for (int step = 0; step < Nt; ++step) {
+    const double t0 = step * dt;
+    for (int i = 0; i < 3; ++i) {
+      const double ti = t0 + ctx->c[i] * dt;
+      const double c = ctx->A[i][i] * dt;
+      Motion mo = motion(ctx, mu, n_mu, ti);
+      FrameT<double> fr = frame_of(mo);
+      // base = u + sum_{j<i} a_ij k_j
+      if (i == 0) PP_TRY(copy(ctx, n, base, u));
+      if (i == 1) PP_TRY(lincomb(ctx, n, base, {1.0, ctx->A[1][0]}, {u, k[0]}));
+      if (i == 2) PP_TRY(lincomb(ctx, n, base, {1.0, ctx->A[2][0], ctx->A[2][1]}, {u, k[0], k[1]}));
+      PP_TRY(copy(ctx, n, k[i], i == 0 ? kprev : k[i - 1]));
+      size_t slot = (size_t)step * 3 + i;
+      double* Js = ctx->st_J + slot * mesh->ne * 4 * nb2(ctx);
+      double* As = ctx->st_Ainv + slot * mesh->ne * nb2(ctx);
+      double* us = ctx->st_u + slot * n;
+      double prev_res = INFINITY;
+      bool converged = false;
+      for (int it = 0; it <= ctx->cfg.newton_maxit; ++it) {
+        PP_TRY(lincomb(ctx, n, us, {1.0, ctx->A[i][i]}, {base, k[i]}));
+        PP_CK(launch_residual(m, ctx->tb, ctx->ph, fr, us, r, ctx->stream));
+        PP_CK(launch_stage_matvec(m, ctx->tb, nullptr, 1.0, 0.0, k[i], R, 0, ctx->stream));
+        PP_TRY(lincomb(ctx, n, R, {1.0, -dt}, {R, r}));
+        double rn, mun;
+        PP_TRY(host_norm(ctx, n, R, &rn));
+        PP_CK(launch_stage_matvec(m, ctx->tb, nullptr, 1.0, 0.0, us, dk, 0, ctx->stream));
+        PP_TRY(host_norm(ctx, n, dk, &mun));
+        // Jacobian and block-Jacobi inverse at the current stage state
+        PP_CK(launch_jacobian(m, ctx->tb, ctx->ph, fr, us, Js, ctx->stream));
+        PP_CK(launch_block_inverse(m, ctx->tb, Js, c, As, ctx->d_status, ctx->stream));
+        const double tol = ctx->cfg.newton_tol * mun;
+        if (rn <= tol || (it > 0 && rn <= 1e3 * tol && rn > 0.5 * prev_res)) {
+          converged = true;
+          break;
+        }
+        if (it == ctx->cfg.newton_maxit) break;
+        prev_res = rn;
+        int gits = 0;
+        StageView sv{Js, As, c};
+        int st = stage_solve(ctx, mesh, sv, 0, R, dk, ctx->cfg.gmres_rtol, 0.0, &gits);
+        if (st != PP_OK && st != PP_ENOCONV) return st;
+        ctx->last_gmres_iters += gits;
+        PP_TRY(lincomb(ctx, n, k[i], {1.0, -1.0}, {k[i], dk}));
+        ctx->last_newton_iters++;
+      }
+      if (!converged) return set_error(ctx, PP_ENOCONV, "stage Newton did not converge");
+      int status = 0;
+      PP_CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      PP_CK(cudaStreamSynchronize(ctx->stream));
+      if (status) {
+        PP_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        return set_error(ctx, PP_ENAN, "singular or non-finite stage block");
+      }
+      // QoI rates at the converged stage
+      PP_CK(launch_qoi(m, ctx->tb, ctx->ph, fr, us, ctx->d_elem, ctx->stream));
+      PP_CK(launch_colsum(mesh->ne, 2, ctx->d_elem, ctx->d_scalar + 8, ctx->d_partial, ctx->d_counter, ctx->stream));
+      PP_CK(cudaMemcpyAsync(ctx->h_scalar + 8, ctx->d_scalar + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+      PP_CK(cudaStreamSynchronize(ctx->stream));
+      ctx->lin_qoi_rates[slot * 2] = ctx->h_scalar[8];
+      ctx->lin_qoi_rates[slot * 2 + 1] = ctx->h_scalar[9];
+    }
+    PP_TRY(lincomb(ctx, n, u, {1.0, ctx->b[0], ctx->b[1], ctx->b[2]}, {u, k[0], k[1], k[2]}));
+    PP_TRY(copy(ctx, n, kprev, k[2]));
+    if (u_traj) PP_TRY(copy(ctx, n, u_traj + (size_t)(step + 1) * n, u));
+  }
+  double W = 0.0, Jx = 0.0;
+  for (int step = 0; step < Nt; ++step)
+    for (int i = 0; i < 3; ++i) {
+      W += dt * ctx->b[i] * ctx->lin_qoi_rates[((size_t)step * 3 + i) * 2];
+      Jx += dt * ctx->b[i] * ctx->lin_qoi_rates[((size_t)step * 3 + i) * 2 + 1];
+    }
+  ctx->lin_W = W;
+  ctx->lin_Jx = Jx;
+  if (qoi) {
+    qoi[0] = W;
+    qoi[1] = Jx;
+    qoi[2] = -W / ctx->cfg.T;
+    qoi[3] = -Jx / ctx->cfg.T;
+  }
+  if (u_final) PP_TRY(copy(ctx, n, u_final, u));
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  ctx->lin_valid = true;
+  return PP_OK;
+}
+
+// --------------------------------------------------------------------------- tangent sweep
+int tangent_sweep(pp_ctx* ctx, const double* v, double* out) {
+  const pp_mesh* mesh = ctx->lin_mesh;
+  const DevMesh& m = mesh->dev;
+  const int64_t n = ctx->ws_nu;
+  const int Nt = ctx->lin_Nt;
+  const double dt = ctx->cfg.T / Nt;
+  double* du = work_vec(ctx, 9);
+  double* dk[3] = {work_vec(ctx, 10), work_vec(ctx, 11), work_vec(ctx, 12)};
+  double* w = work_vec(ctx, 13);
+  double* rhs = work_vec(ctx, 14);
+  double* v0 = work_vec(ctx, 15);
+  PP_TRY(copy(ctx, n, v0, v));
+  PP_TRY(copy(ctx, n, du, v));
+  for (int step = 0; step < Nt; ++step) {
+    for (int i = 0; i < 3; ++i) {
+      StageView sv = stored_stage(ctx, step, i);
+      const double* win = du;
+      if (i == 1) {
+        PP_TRY(lincomb(ctx, n, w, {1.0, ctx->A[1][0]}, {du, dk[0]}));
+        win = w;
+      } else if (i == 2) {
+        PP_TRY(lincomb(ctx, n, w, {1.0, ctx->A[2][0], ctx->A[2][1]}, {du, dk[0], dk[1]}));
+        win = w;
+      }
+      PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 0.0, dt, win, rhs, 0, ctx->stream));
+      int gits = 0;
+      PP_TRY(stage_solve(ctx, mesh, sv, 0, rhs, dk[i], ctx->cfg.lin_rtol, 0.0, &gits));
+    }
+    PP_TRY(lincomb(ctx, n, du, {1.0, ctx->b[0], ctx->b[1], ctx->b[2]}, {du, dk[0], dk[1], dk[2]}));
+  }
+  PP_TRY(lincomb(ctx, n, out, {1.0, -1.0}, {v0, du}));
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  return PP_OK;
+}
+
+// --------------------------------------------------------------------------- adjoint sweep
+int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, double* lam0, double* dFdmu) {
+  const pp_mesh* mesh = ctx->lin_mesh;
+  const DevMesh& m = mesh->dev;
+  const int64_t n = ctx->ws_nu;
+  const int Nt = ctx->lin_Nt;
+  const double dt = ctx->cfg.T / Nt;
+  const int n_mu = (int)ctx->lin_mu.size();
+  const double* mu = ctx->lin_mu.data();
+  double* lam = work_vec(ctx, 16);
+  double* kap = work_vec(ctx, 17);
+  double* y[3] = {work_vec(ctx, 18), work_vec(ctx, 19), work_vec(ctx, 20)};
+  double* g[3] = {work_vec(ctx, 21), work_vec(ctx, 22), work_vec(ctx, 23)};
+  double* rhs = work_vec(ctx, 14);
+  double* dr = work_vec(ctx, 15);
+  const bool withF = weights != nullptr;
+  const double w0 = withF ? weights[0] : 0.0, w1 = withF ? weights[1] : 0.0;
+  std::vector<double> grad(n_mu, 0.0);
+  PP_TRY(copy(ctx, n, lam, lam_Nt));
+  for (int step = Nt - 1; step >= 0; --step) {
+    for (int i = 2; i >= 0; --i) {
+      StageView sv = stored_stage(ctx, step, i);
+      const double ti = step * dt + ctx->c[i] * dt;
+      Motion mo = motion(ctx, mu, n_mu, ti);
+      FrameT<double> fr = frame_of(mo);
+      const double* ui = stored_u(ctx, step, i);
+      // rhs = b_i lam + sum_{j>i} a_ji y_j  (+ dF/dk_i = dt sum_{l>=i} b_l a_li g_l)
+      if (withF) PP_CK(launch_qoi_du(m, ctx->tb, ctx->ph, fr, ui, w0, w1, g[i], ctx->stream));
+      if (i == 2) {
+        PP_TRY(lincomb(ctx, n, rhs, {ctx->b[2]}, {lam}));
+      } else if (i == 1) {
+        PP_TRY(lincomb(ctx, n, rhs, {ctx->b[1], ctx->A[2][1]}, {lam, y[2]}));
+      } else {
+        PP_TRY(lincomb(ctx, n, rhs, {ctx->b[0], ctx->A[1][0], ctx->A[2][0]}, {lam, y[1], y[2]}));
+      }
+      if (withF) {
+        if (i == 2) PP_TRY(lincomb(ctx, n, rhs, {1.0, dt * ctx->b[2] * ctx->A[2][2]}, {rhs, g[2]}));
+        if (i == 1)
+          PP_TRY(lincomb(ctx, n, rhs, {1.0, dt * ctx->b[1] * ctx->A[1][1], dt * ctx->b[2] * ctx->A[2][1]},
+                         {rhs, g[1], g[2]}));
+        if (i == 0)
+          PP_TRY(lincomb(ctx, n, rhs,
+                         {1.0, dt * ctx->b[0] * ctx->A[0][0], dt * ctx->b[1] * ctx->A[1][0],
+                          dt * ctx->b[2] * ctx->A[2][0]},
+                         {rhs, g[0], g[1], g[2]}));
+      }
+      int gits = 0;
+      PP_TRY(stage_solve(ctx, mesh, sv, 1, rhs, kap, ctx->cfg.lin_rtol, 0.0, &gits));
+      PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 0.0, dt, kap, y[i], 1, ctx->stream));
+      if (withF && dFdmu) {
+        // kappa_i . dr/ds and w . dQ/ds for the motion seeds s = theta, theta', h'
+        double sr[3], sq[3];
+        for (int s = 0; s < 3; ++s) {
+          FrameT<Dual> fd;
+          double cth = std::cos(mo.th), sth = std::sin(mo.th);
+          double dQ[4] = {-sth, cth, -cth, -sth};        // dQ/dtheta
+          double d2Q[4] = {-cth, -sth, sth, -cth};        // d2Q/dtheta2
+          for (int k2 = 0; k2 < 4; ++k2) {
+            fd.Q[k2] = Dual(fr.Q[k2], s == 0 ? dQ[k2] : 0.0);
+            fd.Qd[k2] = Dual(fr.Qd[k2], s == 0 ? mo.thd * d2Q[k2] : (s == 1 ? dQ[k2] : 0.0));
+          }
+          fd.hd = Dual(fr.hd, s == 2 ? 1.0 : 0.0);
+          PP_CK(launch_residual_dframe(m, ctx->tb, ctx->ph, fd, ui, dr, ctx->stream));
+          PP_CK(launch_dot(n, kap, dr, ctx->d_scalar + 16 + s, ctx->d_partial, ctx->d_counter, ctx->stream));
+          PP_CK(launch_qoi_dframe(m, ctx->tb, ctx->ph, fd, ui, ctx->d_elem, ctx->stream));
+          PP_CK(launch_colsum(mesh->ne, 2, ctx->d_elem, ctx->d_scalar + 20 + 2 * s, ctx->d_partial, ctx->d_counter,
+                              ctx->stream));
+        }
+        PP_CK(cudaMemcpyAsync(ctx->h_scalar + 16, ctx->d_scalar + 16, 12 * sizeof(double), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+        PP_CK(cudaStreamSynchronize(ctx->stream));
+        for (int s = 0; s < 3; ++s) {
+          sr[s] = ctx->h_scalar[16 + s];
+          sq[s] = w0 * ctx->h_scalar[20 + 2 * s] + w1 * ctx->h_scalar[21 + 2 * s];
+        }
+        for (int j = 0; j < n_mu; ++j) {
+          double ds[3] = {mo.dth[j], mo.dthd[j], mo.dhd[j]};
+          for (int s = 0; s < 3; ++s) grad[j] += dt * sr[s] * ds[s] + dt * ctx->b[i] * sq[s] * ds[s];
+        }
+      }
+    }
+    // lam <- lam + sum_i y_i (+ dF/du^(n-1) = dt sum_l b_l g_l)
+    PP_TRY(lincomb(ctx, n, lam, {1.0, 1.0, 1.0, 1.0}, {lam, y[0], y[1], y[2]}));
+    if (withF)
+      PP_TRY(lincomb(ctx, n, lam, {1.0, dt * ctx->b[0], dt * ctx->b[1], dt * ctx->b[2]}, {lam, g[0], g[1], g[2]}));
+  }
+  PP_TRY(copy(ctx, n, lam0, lam));
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  if (dFdmu)
+    for (int j = 0; j < n_mu; ++j) dFdmu[j] = withF ? grad[j] : 0.0;
+  return PP_OK;
+}
+
+// --------------------------------------------------------------------------- shooting
+int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess, int Nt,
+             double tol, double* u0_out, double* qoi, pp_shoot_stats* stats) {
+  const double t_start = now_s();
+  PP_TRY(ensure_store(ctx, mesh, Nt));
+  const int64_t n = ctx->ws_nu;
+  pp_shoot_stats st{};
+  // u0 lives in u0_out; the outer Krylov level owns V, w, t, r
+  if (u0_guess) {
+    PP_TRY(copy(ctx, n, u0_out, u0_guess));
+  } else {
+    std::vector<double> fs(n);
+    const int nb = ctx->tb.nb, Np = ctx->tb.Np;
+    for (int64_t e = 0; e < mesh->ne; ++e)
+      for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < Np; ++i) fs[e * nb + a * Np + i] = ctx->ph.Uinf[a];
+    PP_CK(cudaMemcpyAsync(u0_out, fs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    PP_CK(cudaStreamSynchronize(ctx->stream));
+  }
+  // outer-level scratch: the last three outer Krylov vectors are free between GMRES calls
+  Krylov& K = ctx->kout;
+  double* uN = K.r;   // reused only outside gmres
+  int status = PP_ENOCONV;
+  for (int it = 0; it <= ctx->cfg.nk_max_newton; ++it) {
+    PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0_out, Nt, nullptr, uN, qoi));
+    st.primal_sweeps++;
+    st.stage_newton_iters += ctx->last_newton_iters;
+    double* R = work_vec(ctx, 4);  // primal-sweep scratch, free now
+    PP_TRY(lincomb(ctx, n, R, {1.0, -1.0}, {uN, u0_out}));
+    double rn;
+    PP_TRY(host_norm(ctx, n, R, &rn));
+    if (it < 64) st.residual[it] = rn;
+    st.newton_iters = it;
+    if (rn <= tol) {
+      status = PP_OK;
+      break;
+    }
+    if (it == ctx->cfg.nk_max_newton) break;
+    // (Phi - I) du = R with matvec (Phi - I) v = -(v - Phi v)
+    double* Rsave = work_vec(ctx, 5);
+    PP_TRY(copy(ctx, n, Rsave, R));
+    double* du = work_vec(ctx, 6);
+    Op A = [&](const double* in, double* out) {
+      PP_TRY(tangent_sweep(ctx, in, out));
+      PP_TRY(lincomb(ctx, n, out, {-1.0}, {out}));
+      return PP_OK;
+    };
+    int kits = 0;
+    int gs = gmres(ctx, K, A, Op(), Rsave, du, ctx->cfg.nk_gmres_rtol, 0.0, ctx->cfg.nk_max_krylov, &kits, nullptr);
+    if (gs != PP_OK && gs != PP_ENOCONV) return gs;
+    st.krylov_iters += kits;
+    PP_TRY(lincomb(ctx, n, u0_out, {1.0, -1.0}, {u0_out, du}));
+  }
+  if (status == PP_OK) {
+    // the stored linearization is that of the returned u0 (the last sweep started from it)
+  }
+  st.seconds = now_s() - t_start;
+  if (stats) *stats = st;
+  if (status != PP_OK) return set_error(ctx, PP_ENOCONV, "shooting did not reach the tolerance");
+  return PP_OK;
+}
+
+// --------------------------------------------------------------------------- periodic adjoint
+int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                     const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats) {
+  const double t_start = now_s();
+  if (u0) {
+    PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0, Nt, nullptr, nullptr, nullptr));
+  } else if (!ctx->lin_valid || ctx->lin_mesh != mesh || ctx->lin_Nt != Nt) {
+    return set_error(ctx, PP_ESTATE, "pp_periodic_adjoint: no matching stored linearization");
+  }
+  const int64_t n = ctx->ws_nu;
+  Krylov& K = ctx->kout;
+  double* d = work_vec(ctx, 4);
+  double* x = work_vec(ctx, 5);
+  double* z = work_vec(ctx, 6);
+  PP_CK(cudaMemsetAsync(z, 0, sizeof(double) * n, ctx->stream));
+  // d = lambda^(0)(0) with the QoI terms; solve (Phi^T - I) x = -d
+  PP_TRY(adjoint_sweep(ctx, z, weights, d, nullptr));
+  PP_TRY(lincomb(ctx, n, d, {-1.0}, {d}));
+  Op A = [&](const double* in, double* out) {
+    PP_TRY(adjoint_sweep(ctx, in, nullptr, out, nullptr));
+    PP_TRY(lincomb(ctx, n, out, {1.0, -1.0}, {out, in}));
+    return PP_OK;
+  };
+  int kits = 0;
+  int gs = gmres(ctx, K, A, Op(), d, x, 0.0, ctx->cfg.adj_tol, ctx->cfg.adj_maxit, &kits, nullptr);
+  if (gs != PP_OK && gs != PP_ENOCONV) return gs;
+  // final sweep with the periodic final condition: multipliers and gradient
+  PP_TRY(adjoint_sweep(ctx, x, weights, z, dFdmu));
+  double res;
+  PP_TRY(lincomb(ctx, n, z, {1.0, -1.0}, {z, x}));
+  PP_TRY(host_norm(ctx, n, z, &res));
+  if (lam_Nt) PP_TRY(copy(ctx, n, lam_Nt, x));
+  if (F) *F = weights[0] * ctx->lin_W + weights[1] * ctx->lin_Jx;
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  if (stats) {
+    stats->krylov_iters = kits;
+    stats->residual = res;
+    stats->seconds = now_s() - t_start;
+  }
+  if (gs == PP_ENOCONV) return set_error(ctx, PP_ENOCONV, "periodic adjoint GMRES hit adj_maxit");
+  return PP_OK;
+}
+
+}  // namespace pp
