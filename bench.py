@@ -178,6 +178,7 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         clocks = clk.stop()
         launches_k, kern_ms = A.pp_prof_read()
+        iters = A.pp_sweep_counts(ctx)
         counts = A.pp_prof_counts()
         ms = ev0.elapsed_time(ev1) / args.steps
 
@@ -208,7 +209,7 @@ def run_ours(args, rank, world, local_rank):
     ms = float(tmax.item())
     A.pp_mesh_destroy(m)
     A.pp_destroy(ctx)
-    return dict(ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, kern_launches=launches_k, kern_ms=kern_ms,
+    return dict(ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, kern_launches=launches_k, kern_ms=kern_ms,
                 counts=counts, e2e=e2e)
 
 
@@ -304,6 +305,7 @@ def main():
         "clocks": res["clocks"],
         "gpu_launches": int(sum(res["counts"].values())),
         "launches_by_class": res["counts"],
+        "last_step_iterations": res["iters"],
     }
     if res["e2e"]:
         e = res["e2e"]

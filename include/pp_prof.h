@@ -32,6 +32,13 @@ int pp_prof_read(int64_t* launches, double* total_ms);
 /* Counts launches of every class since the last pp_prof_select (no events). */
 int pp_prof_counts(int64_t* counts /* [PP_K_COUNT] */);
 
+/* Iteration counts of the last sweeps on ctx: stage Newton iterations and GMRES
+   iterations of the last primal sweep; GMRES iterations of the last tangent and of
+   the last adjoint sweep.  Any pointer may be NULL. */
+struct pp_ctx;
+int pp_sweep_counts(const struct pp_ctx* ctx, int64_t* newton, int64_t* gmres_primal, int64_t* gmres_tangent,
+                    int64_t* gmres_adjoint);
+
 /* Measures the device's FP64 FMA throughput (TFLOP/s, 2 flops per FMA) with an
    unrolled dependent-chain kernel over all SMs; returns PP_OK or PP_ECUDA. */
 int pp_measure_fp64_peak(int device, double* tflops);

@@ -24,7 +24,7 @@ EXPORTED = [
     "pp_mesh_destroy", "pp_mesh_info", "pp_residual", "pp_jacobian_blocks", "pp_qoi_rate", "pp_primal_period",
     "pp_tangent_matvec", "pp_adjoint_sweep", "pp_shoot_nk", "pp_periodic_adjoint",
     # include/pp_prof.h
-    "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak",
+    "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
 ]
 PP_K = dict(none=0, jacobian=1, residual=2, stage_matvec=3, block_apply=4, block_inverse=5, krylov=6, other=7)
 
@@ -82,6 +82,7 @@ def _load():
         "pp_prof_read": (I, [C.POINTER(C.c_int64), dp]),
         "pp_prof_counts": (I, [C.POINTER(C.c_int64)]),
         "pp_measure_fp64_peak": (I, [I, dp]),
+        "pp_sweep_counts": (I, [P] + [C.POINTER(C.c_int64)] * 4),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,3 +260,9 @@ def pp_measure_fp64_peak(device=0):
     t = C.c_double()
     _check(None, _lib.pp_measure_fp64_peak(int(device), C.byref(t)))
     return t.value
+
+
+def pp_sweep_counts(ctx):
+    v = [C.c_int64() for _ in range(4)]
+    _check(ctx, _lib.pp_sweep_counts(ctx, *[C.byref(x) for x in v]))
+    return dict(newton=v[0].value, gmres_primal=v[1].value, gmres_tangent=v[2].value, gmres_adjoint=v[3].value)

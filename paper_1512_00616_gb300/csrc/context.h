@@ -32,10 +32,17 @@ struct Krylov {
   double* w = nullptr;   // [n]
   double* t = nullptr;   // [n]
   double* r = nullptr;   // [n]
-  double* d_h = nullptr; // [2*(m+1) + 2] device: h1 | h2 | norm2 | y
-  double* h_h = nullptr; // pinned mirror
+  double* d_h = nullptr; // device: h1 [m+2] | h2 [m+2] | norm2 | y | H [(m+1) m] | cs | sn | g | stat [8]
+  double* h_h = nullptr; // pinned ring of stat copies [kRing][8]
   double* d_y = nullptr; // [m+1]
+  double* d_H = nullptr;
+  double* d_cs = nullptr;
+  double* d_sn = nullptr;
+  double* d_g = nullptr;
+  double* d_stat = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
+constexpr int kRing = 4;
 
 // Motion quantities at one time and their derivatives w.r.t. mu.
 struct Motion {
@@ -85,8 +92,10 @@ struct pp_ctx {
   double* st_u = nullptr;       // [stages][nu] stage states
   std::vector<double> lin_qoi_rates;  // [Nt*3][2]
   double lin_W = 0.0, lin_Jx = 0.0;
-  int last_newton_iters = 0;
-  int last_gmres_iters = 0;
+  int64_t last_newton_iters = 0;
+  int64_t last_gmres_iters = 0;
+  int64_t last_gmres_tangent = 0;
+  int64_t last_gmres_adjoint = 0;
 };
 
 namespace pp {

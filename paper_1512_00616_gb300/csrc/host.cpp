@@ -12,6 +12,7 @@
 #include <utility>
 
 #include "context.h"
+#include "../../include/pp_prof.h"
 
 namespace pp {
 
@@ -224,9 +225,18 @@ static int alloc_krylov(pp_ctx* ctx, Krylov& k, int m, int64_t n) {
   k.w = k.V + (size_t)(m + 1) * n;
   k.t = k.w + n;
   k.r = k.t + n;
-  PP_CK(cudaMalloc(&k.d_h, sizeof(double) * (3 * (m + 2) + 8)));
-  PP_CK(cudaMallocHost(&k.h_h, sizeof(double) * (3 * (m + 2) + 8)));
+  const size_t nh = 2 * (m + 2) + 4 + (m + 2) + (size_t)(m + 1) * m + 3 * (m + 2) + 16;
+  PP_CK(cudaMalloc(&k.d_h, sizeof(double) * nh));
+  PP_CK(cudaMemset(k.d_h, 0, sizeof(double) * nh));
+  PP_CK(cudaMallocHost(&k.h_h, sizeof(double) * 8 * kRing + 64));
   k.d_y = k.d_h + 2 * (m + 2) + 4;
+  k.d_H = k.d_y + (m + 2);
+  k.d_cs = k.d_H + (size_t)(m + 1) * m;
+  k.d_sn = k.d_cs + (m + 2);
+  k.d_g = k.d_sn + (m + 2);
+  k.d_stat = k.d_g + (m + 2);
+  for (int i = 0; i < kRing; ++i)
+    if (!k.ev[i]) PP_CK(cudaEventCreateWithFlags(&k.ev[i], cudaEventDisableTiming));
   return PP_OK;
 }
 
@@ -411,6 +421,8 @@ int pp_destroy(pp_ctx* ctx) {
     cudaFree(k->V);
     cudaFree(k->d_h);
     if (k->h_h) cudaFreeHost(k->h_h);
+    for (int i = 0; i < kRing; ++i)
+      if (k->ev[i]) cudaEventDestroy(k->ev[i]);
   }
   cudaFree(ctx->st_J);
   cudaFree(ctx->st_Ainv);
@@ -531,6 +543,16 @@ int pp_mesh_create(pp_ctx* ctx, const double* verts, int nv, const int32_t* tris
   d.nbrface = m->d_int + 3 * nt;
   d.tag = m->d_int + 6 * nt;
   *out = m;
+  return PP_OK;
+}
+
+int pp_sweep_counts(const pp_ctx* ctx, int64_t* newton, int64_t* gmres_primal, int64_t* gmres_tangent,
+                    int64_t* gmres_adjoint) {
+  if (!ctx) return PP_EINVAL;
+  if (newton) *newton = ctx->last_newton_iters;
+  if (gmres_primal) *gmres_primal = ctx->last_gmres_iters;
+  if (gmres_tangent) *gmres_tangent = ctx->last_gmres_tangent;
+  if (gmres_adjoint) *gmres_adjoint = ctx->last_gmres_adjoint;
   return PP_OK;
 }
 

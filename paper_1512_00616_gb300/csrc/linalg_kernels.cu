@@ -24,7 +24,6 @@ constexpr int INV_THREADS = 256;
 constexpr int MV_WARPS = 4;
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
-constexpr int kChunk = 4;
 
 __global__ void __launch_bounds__(INV_THREADS)
     k_block_inverse(DevMesh m, DevTables tb, const double* __restrict__ J, double c, double* __restrict__ Ainv,
@@ -115,84 +114,190 @@ __global__ void __launch_bounds__(INV_THREADS)
   }
 }
 
-// y_e = alpha M_e x_e + beta (J x)_e  or  beta (J^T x)_e
-__global__ void __launch_bounds__(MV_WARPS * 32)
-    k_stage_matvec(DevMesh m, DevTables tb, const double* __restrict__ J, double alpha, double beta,
-                   const double* __restrict__ x, double* __restrict__ y, int trans) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * MV_WARPS + warp;
-  if (e >= m.ne) return;
-  const int nb = tb.nb, Np = tb.Np;
-  const size_t nb2 = (size_t)nb * nb;
-  const double* xe = x + (size_t)e * nb;
-  for (int r = lane; r < nb; r += 32) {
-    double acc = 0.0;
-    if (alpha != 0.0) {
-      int a = r / Np, i = r - a * Np;
-      double s = 0.0;
-      for (int j = 0; j < Np; ++j) s += tb.Mref[i * Np + j] * xe[a * Np + j];
-      acc = alpha * m.detB[e] * s;
-    }
-    if (beta != 0.0) {
-      double s = 0.0;
-      if (!trans) {
-        for (int slot = 0; slot < 4; ++slot) {
-          int src = e;
-          if (slot > 0) {
-            src = m.nbr[3 * e + slot - 1];
-            if (src < 0) continue;
-          }
-          const double* Jb = J + ((size_t)e * 4 + slot) * nb2 + r;
-          const double* xs = x + (size_t)src * nb;
-          for (int cc = 0; cc < nb; ++cc) s += Jb[(size_t)cc * nb] * xs[cc];
-        }
-      } else {
-        const double* Jb = J + ((size_t)e * 4) * nb2 + (size_t)r * nb;
-        for (int cc = 0; cc < nb; ++cc) s += Jb[cc] * xe[cc];
-        for (int f = 0; f < 3; ++f) {
-          int e2 = m.nbr[3 * e + f];
-          if (e2 < 0) continue;
-          int g = m.nbrface[3 * e + f];
-          const double* J2 = J + ((size_t)e2 * 4 + 1 + g) * nb2 + (size_t)r * nb;
-          const double* x2 = x + (size_t)e2 * nb;
-          for (int cc = 0; cc < nb; ++cc) s += J2[cc] * x2[cc];
-        }
+// Warp reduce-scatter of KB (power of two, <= 32) per-lane values: afterwards lane l
+// holds the warp sum of value (l >> (5 - log2 KB)) in v[0] (31 shuffles for KB = 32).
+template <int CNT, int O>
+__device__ __forceinline__ void rs_step(double* v, int lane) {
+  if constexpr (O > 0) {
+    if constexpr (CNT > 1) {
+      constexpr int half = CNT / 2;
+      const bool upper = (lane & O) != 0;
+#pragma unroll
+      for (int t = 0; t < half; ++t) {
+        const double send = upper ? v[t] : v[t + half];
+        const double keep = upper ? v[t + half] : v[t];
+        v[t] = keep + __shfl_xor_sync(0xffffffffu, send, O);
       }
-      acc += beta * s;
+      rs_step<half, O / 2>(v, lane);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+      rs_step<1, O / 2>(v, lane);
     }
-    y[(size_t)e * nb + r] = acc;
   }
 }
 
+template <int KB>
+__device__ __forceinline__ void warp_reduce_scatter(double* v, int lane) {
+  rs_step<KB, 16>(v, lane);
+}
+
+template <int KB>
+struct ILog2 {
+  static constexpr int value = KB >= 32 ? 5 : KB >= 16 ? 4 : KB >= 8 ? 3 : KB >= 4 ? 2 : KB >= 2 ? 1 : 0;
+};
+
+// Warp-per-element block products with compile-time block size NB = 4 Np.
+// Normal: lanes over rows, inputs broadcast by shuffles, columns streamed (column-major,
+// coalesced).  Transposed: output r is the dot product of the contiguous column r with
+// the input, so lanes run over the column and a reduce-scatter across the warp delivers
+// 32 outputs at a time.
+template <int NB>
+struct BlockOps {
+  static constexpr int H = (NB + 31) / 32;
+
+  __device__ static __forceinline__ void load(const double* x, int lane, double xr[H]) {
+#pragma unroll
+    for (int h = 0; h < H; ++h) xr[h] = (lane + 32 * h < NB) ? x[lane + 32 * h] : 0.0;
+  }
+
+  // acc[h] += (B x)[lane + 32h], B column-major NB x NB
+  __device__ static __forceinline__ void mv(const double* __restrict__ B, const double xr[H], int lane,
+                                            double acc[H]) {
+#pragma unroll 8
+    for (int c = 0; c < NB; ++c) {
+      const double xc = __shfl_sync(0xffffffffu, xr[c >> 5], c & 31);
+#pragma unroll
+      for (int h = 0; h < H; ++h)
+        if (lane + 32 * h < NB) acc[h] += B[(size_t)c * NB + lane + 32 * h] * xc;
+    }
+  }
+
+  // out[h] = sum_q (B_q^T x_q)[lane + 32h] over NQ blocks (null blocks skipped)
+  template <int NQ>
+  __device__ static __forceinline__ void mvt(const double* const (&Bq)[NQ], const double (&xq)[NQ][H], int lane,
+                                             double out[H]) {
+#pragma unroll
+    for (int b = 0; b < H; ++b) {
+      constexpr int KB = 32;
+      double acc[KB];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) acc[t] = 0.0;
+      const int r0 = 32 * b;
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        if (r0 + t < NB) {
+          double part = 0.0;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            if (!Bq[q]) continue;
+            const double* col = Bq[q] + (size_t)(r0 + t) * NB;
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+              if (lane + 32 * h < NB) part += col[lane + 32 * h] * xq[q][h];
+          }
+          acc[t] = part;
+        }
+      }
+      warp_reduce_scatter<KB>(acc, lane);
+      out[b] = acc[0];
+    }
+  }
+};
+
+template <int NB>
 __global__ void __launch_bounds__(MV_WARPS * 32)
-    k_block_apply(int ne, int nb, const double* __restrict__ Ainv, const double* __restrict__ x,
-                  double* __restrict__ y, int trans) {
+    k_stage_matvec(DevMesh m, DevTables tb, const double* __restrict__ J, double alpha, double beta,
+                   const double* __restrict__ x, double* __restrict__ y, int trans) {
+  using Ops = BlockOps<NB>;
+  constexpr int H = Ops::H;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * MV_WARPS + warp;
+  if (e >= m.ne) return;
+  const int Np = NB / 4;
+  constexpr size_t nb2 = (size_t)NB * NB;
+  const double* xe = x + (size_t)e * NB;
+  double acc[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    acc[h] = 0.0;
+    const int r = lane + 32 * h;
+    if (alpha != 0.0 && r < NB) {
+      const int a = r / Np, i = r - a * Np;
+      double s = 0.0;
+      for (int j = 0; j < Np; ++j) s += tb.Mref[i * Np + j] * xe[a * Np + j];
+      acc[h] = alpha * m.detB[e] * s;
+    }
+  }
+  if (beta != 0.0) {
+    double s[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) s[h] = 0.0;
+    if (!trans) {
+      for (int slot = 0; slot < 4; ++slot) {
+        int src = e;
+        if (slot > 0) {
+          src = m.nbr[3 * e + slot - 1];
+          if (src < 0) continue;
+        }
+        double xr[H];
+        Ops::load(x + (size_t)src * NB, lane, xr);
+        Ops::mv(J + ((size_t)e * 4 + slot) * nb2, xr, lane, s);
+      }
+    } else {
+      // (J^T x)_e = J_ee^T x_e + sum_f J_{e2,e}^T x_e2, J_{e2,e} = slot (1 + nbrface) of e2
+      const double* Bq[4];
+      double xq[4][H];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double* src = xe;
+        Bq[q] = nullptr;
+        if (q == 0) {
+          Bq[q] = J + ((size_t)e * 4) * nb2;
+        } else {
+          const int e2 = m.nbr[3 * e + q - 1];
+          if (e2 >= 0) {
+            Bq[q] = J + ((size_t)e2 * 4 + 1 + m.nbrface[3 * e + q - 1]) * nb2;
+            src = x + (size_t)e2 * NB;
+          }
+        }
+        Ops::load(src, lane, xq[q]);
+      }
+      Ops::template mvt<4>(Bq, xq, lane, s);
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) acc[h] += beta * s[h];
+  }
+#pragma unroll
+  for (int h = 0; h < H; ++h)
+    if (lane + 32 * h < NB) y[(size_t)e * NB + lane + 32 * h] = acc[h];
+}
+
+template <int NB>
+__global__ void __launch_bounds__(MV_WARPS * 32)
+    k_block_apply(int ne, const double* __restrict__ Ainv, const double* __restrict__ x, double* __restrict__ y,
+                  int trans) {
+  using Ops = BlockOps<NB>;
+  constexpr int H = Ops::H;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x * MV_WARPS + warp;
   if (e >= ne) return;
-  const size_t nb2 = (size_t)nb * nb;
-  const double* A = Ainv + (size_t)e * nb2;
-  const double* xe = x + (size_t)e * nb;
-  double acc[2] = {0.0, 0.0};
+  const double* A = Ainv + (size_t)e * NB * NB;
+  double acc[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) acc[h] = 0.0;
   if (!trans) {
-    for (int cc = 0; cc < nb; ++cc) {
-      double xc = xe[cc];
-      if (lane < nb) acc[0] += A[(size_t)cc * nb + lane] * xc;
-      if (lane + 32 < nb) acc[1] += A[(size_t)cc * nb + lane + 32] * xc;
-    }
+    double xr[H];
+    Ops::load(x + (size_t)e * NB, lane, xr);
+    Ops::mv(A, xr, lane, acc);
   } else {
-    for (int h = 0; h < 2; ++h) {
-      int r = lane + 32 * h;
-      if (r >= nb) break;
-      const double* Ar = A + (size_t)r * nb;
-      double s = 0.0;
-      for (int cc = 0; cc < nb; ++cc) s += Ar[cc] * xe[cc];
-      acc[h] = s;
-    }
+    const double* Bq[1] = {A};
+    double xq[1][H];
+    Ops::load(x + (size_t)e * NB, lane, xq[0]);
+    Ops::template mvt<1>(Bq, xq, lane, acc);
   }
-  __syncwarp();
-  if (lane < nb) y[(size_t)e * nb + lane] = acc[0];
-  if (lane + 32 < nb) y[(size_t)e * nb + lane + 32] = acc[1];
+#pragma unroll
+  for (int h = 0; h < H; ++h)
+    if (lane + 32 * h < NB) y[(size_t)e * NB + lane + 32 * h] = acc[h];
 }
 
 __global__ void k_lincomb(int64_t n, double* y, int nterms, double c0, double c1, double c2, double c3,
@@ -211,22 +316,20 @@ __global__ void k_scale(int64_t n, double* y, double a, const double* x) {
     y[i] = a * x[i];
 }
 
-// block-wide sum of k <= kChunk values; result valid in thread 0
-__device__ __forceinline__ void block_sum(double* v, int k, double (*sh)[RED_THREADS / 32]) {
+// block partial sums of KB per-thread values -> partial[blockIdx*ld + j0 + t], t < kb
+template <int KB>
+__device__ __forceinline__ void block_partials(double* v, int kb, double* partial, int ld, int j0) {
+  __shared__ double red[32][RED_THREADS / 32 + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = 0; j < k; ++j) {
-    double s = v[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) sh[j][warp] = s;
-  }
+  warp_reduce_scatter<KB>(v, lane);
+  constexpr int sh = 5 - ILog2<KB>::value;
+  if ((lane & ((1 << sh) - 1)) == 0) red[lane >> sh][warp] = v[0];
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int j = 0; j < k; ++j) {
-      double s = 0.0;
-      for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[j][w];
-      v[j] = s;
-    }
+  if (threadIdx.x < kb) {
+    double s = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) s += red[threadIdx.x][w];
+    partial[(size_t)blockIdx.x * ld + j0 + threadIdx.x] = s;
+  }
   __syncthreads();
 }
 
@@ -234,6 +337,7 @@ __device__ __forceinline__ void block_sum(double* v, int k, double (*sh)[RED_THR
 __device__ __forceinline__ void finish(int k, double* partial, unsigned* counter, double* out) {
   __shared__ bool last;
   __threadfence();
+  __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
@@ -246,11 +350,40 @@ __device__ __forceinline__ void finish(int k, double* partial, unsigned* counter
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// dot products of w with vectors V_{j0..j0+kb-1} accumulated over this thread's indices
+template <int KB>
+__device__ __forceinline__ void dots_batch(int64_t n, const double* __restrict__ V, int64_t ldv, int j0, int kb,
+                                           const double* w, double* partial, int ld) {
+  double acc[KB];
+#pragma unroll
+  for (int t = 0; t < KB; ++t) acc[t] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += stride) {
+    const double wi = w[i];
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (t < kb) acc[t] += V[(int64_t)(j0 + t) * ldv + i] * wi;
+  }
+  block_partials<KB>(acc, kb, partial, ld, j0);
+}
+
+__device__ __forceinline__ void dots_any(int64_t n, const double* V, int64_t ldv, int k, const double* w,
+                                         double* partial) {
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    const int kb = min(32, k - j0);
+    if (kb > 16) dots_batch<32>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 8) dots_batch<16>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 4) dots_batch<8>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 2) dots_batch<4>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 1) dots_batch<2>(n, V, ldv, j0, kb, w, partial, k);
+    else dots_batch<1>(n, V, ldv, j0, kb, w, partial, k);
+  }
+}
+
 // mode 0: out = V^T w;  mode 1: w -= V h, out = V^T w;  mode 2: w -= V h, out[0] = w.w;  mode 3: out[0] = V_0 . w
 __global__ void __launch_bounds__(RED_THREADS)
     k_krylov(int mode, int64_t n, const double* __restrict__ V, int64_t ldv, int k, const double* __restrict__ h,
              double* __restrict__ w, double* __restrict__ out, double* __restrict__ partial, unsigned* counter) {
-  __shared__ double sh[kChunk][RED_THREADS / 32];
   const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
   const int64_t i0 = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x;
   if (mode == 1 || mode == 2) {
@@ -260,39 +393,95 @@ __global__ void __launch_bounds__(RED_THREADS)
       w[i] = s;
     }
   }
-  const int nout = (mode == 2 || mode == 3) ? 1 : k;
-  for (int j0 = 0; j0 < nout; j0 += kChunk) {
-    int kc = min(kChunk, nout - j0);
-    double acc[kChunk] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t i = i0; i < n; i += stride) {
-      double wi = w[i];
-      if (mode == 2) {
-        acc[0] += wi * wi;
-      } else {
-        for (int j = 0; j < kc; ++j) acc[j] += V[(j0 + j) * ldv + i] * wi;
-      }
-    }
-    block_sum(acc, kc, sh);
-    if (threadIdx.x == 0)
-      for (int j = 0; j < kc; ++j) partial[(size_t)blockIdx.x * nout + j0 + j] = acc[j];
+  if (mode == 2) {
+    dots_batch<1>(n, w, 0, 0, 1, w, partial, 1);
+    finish(1, partial, counter, out);
+    return;
   }
-  finish(nout, partial, counter, out);
+  if (mode == 3) {
+    dots_batch<1>(n, V, 0, 0, 1, w, partial, 1);
+    finish(1, partial, counter, out);
+    return;
+  }
+  dots_any(n, V, ldv, k, w, partial);
+  finish(k, partial, counter, out);
 }
 
-// out[j] = sum_e per_elem[e*k + j]
+// out[j] = sum_e per_elem[e*k + j], k <= 8
 __global__ void __launch_bounds__(RED_THREADS)
     k_colsum(int ne, int k, const double* __restrict__ pe, double* out, double* partial, unsigned* counter) {
-  __shared__ double sh[kChunk][RED_THREADS / 32];
-  for (int j0 = 0; j0 < k; j0 += kChunk) {
-    int kc = min(kChunk, k - j0);
-    double acc[kChunk] = {0.0, 0.0, 0.0, 0.0};
-    for (int e = blockIdx.x * RED_THREADS + threadIdx.x; e < ne; e += gridDim.x * RED_THREADS)
-      for (int j = 0; j < kc; ++j) acc[j] += pe[(size_t)e * k + j0 + j];
-    block_sum(acc, kc, sh);
-    if (threadIdx.x == 0)
-      for (int j = 0; j < kc; ++j) partial[(size_t)blockIdx.x * k + j0 + j] = acc[j];
-  }
+  double acc[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) acc[t] = 0.0;
+  for (int e = blockIdx.x * RED_THREADS + threadIdx.x; e < ne; e += gridDim.x * RED_THREADS)
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (t < k) acc[t] += pe[(size_t)e * k + t];
+  block_partials<8>(acc, k, partial, k, 0);
   finish(k, partial, counter, out);
+}
+
+__global__ void k_scale_dev(int64_t n, double* y, const double* a, const double* x) {
+  const double s = a[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = s * x[i];
+}
+
+// GMRES bookkeeping on the device (one thread): stat = {res, tol, hn, inv_hn, beta, inv_beta, flag, j}
+__global__ void k_gmres_init(const double* bb, double rtol, double atol, int first, int m, double* g, double* stat) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double beta = sqrt(fmax(bb[0], 0.0));
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  if (first) stat[1] = fmax(rtol * beta, atol);
+  stat[0] = beta;
+  stat[4] = beta;
+  stat[5] = beta > 0.0 ? 1.0 / beta : 0.0;
+  stat[6] = (beta <= stat[1]) ? 1.0 : 0.0;
+  if (!isfinite(beta)) stat[6] = 4.0;
+  stat[7] = -1.0;
+}
+
+__global__ void k_gmres_givens(int j, int m, const double* h1, const double* h2, const double* nrm2, double* H,
+                               double* cs, double* sn, double* g, double* stat) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* col = H + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn = sqrt(fmax(nrm2[0], 0.0));
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rr = hypot(col[j], col[j + 1]);
+  cs[j] = rr > 0.0 ? col[j] / rr : 1.0;
+  sn[j] = rr > 0.0 ? col[j + 1] / rr : 0.0;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  const double res = fabs(g[j + 1]);
+  stat[0] = res;
+  stat[2] = hn;
+  stat[3] = hn > 0.0 ? 1.0 / hn : 0.0;
+  double flag = 0.0;
+  if (res <= stat[1]) flag = 1.0;
+  if (hn == 0.0) flag = 2.0;
+  if (!isfinite(hn) || !isfinite(res)) flag = 4.0;
+  stat[6] = flag;
+  stat[7] = (double)j;
+}
+
+// y = -(H^{-1} g) on the leading ncols x ncols triangle (negated for the fused update kernel)
+__global__ void k_gmres_backsolve(int ncols, int m, const double* H, const double* g, double* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = ncols - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int k = i + 1; k < ncols; ++k) s += H[(size_t)k * (m + 1) + i] * y[k];  // y holds negated values
+    const double d = H[(size_t)i * (m + 1) + i];
+    y[i] = d != 0.0 ? -s / d : 0.0;
+  }
 }
 
 int vec_blocks(int64_t n) {
@@ -319,14 +508,28 @@ cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const do
 cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const double* J, double alpha, double beta,
                                 const double* x, double* y, int trans, cudaStream_t st) {
   ProfScope ps(PP_K_STAGE_MATVEC, st);
-  k_stage_matvec<<<(m.ne + MV_WARPS - 1) / MV_WARPS, MV_WARPS * 32, 0, st>>>(m, tb, J, alpha, beta, x, y, trans);
+  const int g = (m.ne + MV_WARPS - 1) / MV_WARPS, b = MV_WARPS * 32;
+  switch (tb.nb) {
+    case 12: k_stage_matvec<12><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
+    case 24: k_stage_matvec<24><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
+    case 40: k_stage_matvec<40><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
+    case 60: k_stage_matvec<60><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_block_apply(const DevMesh& m, int nb, const double* Ainv, const double* x, double* y, int trans,
                                cudaStream_t st) {
   ProfScope ps(PP_K_BLOCK_APPLY, st);
-  k_block_apply<<<(m.ne + MV_WARPS - 1) / MV_WARPS, MV_WARPS * 32, 0, st>>>(m.ne, nb, Ainv, x, y, trans);
+  const int g = (m.ne + MV_WARPS - 1) / MV_WARPS, b = MV_WARPS * 32;
+  switch (nb) {
+    case 12: k_block_apply<12><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
+    case 24: k_block_apply<24><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
+    case 40: k_block_apply<40><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
+    case 60: k_block_apply<60><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -336,6 +539,32 @@ cudaError_t launch_lincomb(int64_t n, double* y, int nterms, const double* c, co
   k_lincomb<<<vec_blocks(n), 256, 0, st>>>(n, y, nterms, c[0], nterms > 1 ? c[1] : 0.0, nterms > 2 ? c[2] : 0.0,
                                            nterms > 3 ? c[3] : 0.0, x[0], nterms > 1 ? x[1] : nullptr,
                                            nterms > 2 ? x[2] : nullptr, nterms > 3 ? x[3] : nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_dev(int64_t n, double* y, const double* a, const double* x, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_scale_dev<<<vec_blocks(n), 256, 0, st>>>(n, y, a, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_init(const double* bb, double rtol, double atol, int first, int m, double* g, double* stat,
+                              cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_gmres_init<<<1, 32, 0, st>>>(bb, rtol, atol, first, m, g, stat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_givens(int j, int m, const double* h1, const double* h2, const double* nrm2, double* H,
+                                double* cs, double* sn, double* g, double* stat, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_gmres_givens<<<1, 32, 0, st>>>(j, m, h1, h2, nrm2, H, cs, sn, g, stat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_backsolve(int ncols, int m, const double* H, const double* g, double* y, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_gmres_backsolve<<<1, 32, 0, st>>>(ncols, m, H, g, y);
   return cudaGetLastError();
 }
 

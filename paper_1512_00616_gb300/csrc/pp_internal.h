@@ -141,6 +141,13 @@ cudaError_t launch_block_apply(const DevMesh& m, int nb, const double* Ainv, con
 cudaError_t launch_lincomb(int64_t n, double* y, int nterms, const double* c, const double* const* x,
                            cudaStream_t st);  // y = sum c_k x_k (y may alias one x_k)
 cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaStream_t st);  // y = a x
+cudaError_t launch_scale_dev(int64_t n, double* y, const double* a, const double* x, cudaStream_t st);  // y = a[0] x
+// device-side GMRES bookkeeping; stat = {res, tol, hn, 1/hn, beta, 1/beta, flag, j}
+cudaError_t launch_gmres_init(const double* bb, double rtol, double atol, int first, int m, double* g, double* stat,
+                              cudaStream_t st);
+cudaError_t launch_gmres_givens(int j, int m, const double* h1, const double* h2, const double* nrm2, double* H,
+                                double* cs, double* sn, double* g, double* stat, cudaStream_t st);
+cudaError_t launch_gmres_backsolve(int ncols, int m, const double* H, const double* g, double* y, cudaStream_t st);
 // out[j] = V_j . w for j < k, V contiguous with stride ldv; deterministic two-level reduction
 cudaError_t launch_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* w, double* out,
                         double* partial, unsigned* counter, cudaStream_t st);

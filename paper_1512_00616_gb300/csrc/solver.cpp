@@ -69,31 +69,35 @@ int copy(pp_ctx* ctx, int64_t n, double* y, const double* x) {
 }
 
 // Right-preconditioned restarted GMRES for A x = b, x0 = 0.  Stops when
-// ||b - A x|| <= max(rtol ||b||, atol) (Arnoldi estimate) or after maxit
-// Krylov steps.  prec may be empty (no preconditioner).
+// ||b - A x|| <= max(rtol ||b||, atol) (Arnoldi estimate) or after maxit Krylov
+// steps.  prec may be empty (no preconditioner).
+//
+// The Hessenberg column, Givens rotations and residual estimate are kept on the
+// device; the host watches the convergence flag one Arnoldi step behind (event +
+// pinned copy per step), so the GPU queue never drains for a round trip.  The step
+// enqueued past convergence is simply not used (its column is beyond ncols).
 int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, double* x, double rtol, double atol,
           int maxit, int* iters, double* res_out) {
   const int64_t n = K.n;
   const int m = K.m;
-  double bnorm;
-  PP_TRY(host_norm(ctx, n, b, &bnorm));
+  double* d_h1 = K.d_h;
+  double* d_h2 = K.d_h + (m + 2);
+  double* d_nrm = K.d_h + 2 * (m + 2);
   PP_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
-  if (iters) *iters = 0;
-  if (res_out) *res_out = bnorm;
-  if (bnorm == 0.0) return PP_OK;
-  const double tol = std::fmax(rtol * bnorm, atol);
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
-  int total = 0;
-  double beta = bnorm;
   PP_TRY(copy(ctx, n, K.r, b));
-  bool done = false;
-  while (!done) {
-    PP_CK(launch_scale(n, K.V, 1.0 / beta, K.r, ctx->stream));
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int j = 0;
-    double res = beta;
-    for (; j < m; ++j) {
+  int total = 0;
+  bool first = true;
+  double res = 0.0;
+  int status = PP_ENOCONV;
+  for (;;) {
+    // beta = ||r||, g = beta e1, tolerance fixed on the first cycle
+    PP_CK(launch_dot(n, K.r, K.r, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
+    PP_CK(launch_gmres_init(d_nrm, rtol, atol, first ? 1 : 0, m, K.d_g, K.d_stat, ctx->stream));
+    PP_CK(launch_scale_dev(n, K.V, K.d_stat + 5, K.r, ctx->stream));
+    first = false;
+    int ncols = 0;
+    double flag = 0.0;
+    for (int j = 0; j < m; ++j) {
       double* vj = K.V + (size_t)j * n;
       const double* z = vj;
       if (prec) {
@@ -101,76 +105,51 @@ int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, 
         z = K.t;
       }
       PP_TRY(A(z, K.w));
-      double* d_h1 = K.d_h;
-      double* d_h2 = K.d_h + (m + 2);
-      double* d_nrm = K.d_h + 2 * (m + 2);
       PP_CK(launch_mdot(n, K.V, n, j + 1, K.w, d_h1, ctx->d_partial, ctx->d_counter, ctx->stream));
       PP_CK(launch_update_mdot(n, K.V, n, j + 1, d_h1, K.w, d_h2, ctx->d_partial, ctx->d_counter, ctx->stream));
       PP_CK(launch_update_norm2(n, K.V, n, j + 1, d_h2, K.w, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
-      PP_CK(cudaMemcpyAsync(K.h_h, K.d_h, sizeof(double) * (2 * (m + 2) + 1), cudaMemcpyDeviceToHost, ctx->stream));
-      PP_CK(cudaStreamSynchronize(ctx->stream));
-      double* col = &H[(size_t)j * (m + 1)];
-      for (int i = 0; i <= j; ++i) col[i] = K.h_h[i] + K.h_h[(m + 2) + i];
-      double hn = std::sqrt(std::fmax(K.h_h[2 * (m + 2)], 0.0));
-      if (!std::isfinite(hn)) return set_error(ctx, PP_ENAN, "GMRES: non-finite Arnoldi norm");
-      col[j + 1] = hn;
-      for (int i = 0; i < j; ++i) {
-        double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
-      }
-      double rr = std::hypot(col[j], col[j + 1]);
-      cs[j] = rr > 0 ? col[j] / rr : 1.0;
-      sn[j] = rr > 0 ? col[j + 1] / rr : 0.0;
-      col[j] = rr;
-      col[j + 1] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      res = std::fabs(g[j + 1]);
+      PP_CK(launch_gmres_givens(j, m, d_h1, d_h2, d_nrm, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
+      double* slot = K.h_h + 8 * (j % kRing);
+      PP_CK(cudaMemcpyAsync(slot, K.d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
+      PP_CK(launch_scale_dev(n, K.V + (size_t)(j + 1) * n, K.d_stat + 3, K.w, ctx->stream));
       ++total;
-      bool stop = res <= tol || total >= maxit || hn == 0.0;
-      if (!stop) PP_CK(launch_scale(n, K.V + (size_t)(j + 1) * n, 1.0 / hn, K.w, ctx->stream));
-      if (stop) {
-        ++j;
+      // look one step behind
+      const int jl = (j == m - 1) ? j : j - 1;
+      if (jl < 0) continue;
+      PP_CK(cudaEventSynchronize(K.ev[jl % kRing]));
+      const double* st = K.h_h + 8 * (jl % kRing);
+      flag = st[6];
+      res = st[0];
+      if (flag >= 4.0) return set_error(ctx, PP_ENAN, "GMRES: non-finite Arnoldi quantity");
+      if (flag > 0.0 || total - (j - jl) >= maxit || j == m - 1) {
+        ncols = jl + 1;
         break;
       }
     }
-    if (j > m) j = m;
-    // back substitution H y = g on the j x j upper triangle
-    for (int i = j - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int k = i + 1; k < j; ++k) s -= H[(size_t)k * (m + 1) + i] * y[k];
-      y[i] = s / H[(size_t)i * (m + 1) + i];
-    }
-    // x += P^{-1} V y: t = V y via the fused update kernel (w := 0 - V(-y))
-    for (int i = 0; i < j; ++i) K.h_h[i] = -y[i];
-    PP_CK(cudaMemcpyAsync(K.d_y, K.h_h, sizeof(double) * j, cudaMemcpyHostToDevice, ctx->stream));
+    if (ncols == 0) ncols = 1;  // m == 1 corner: one column
+    // x += P^{-1} V y
+    PP_CK(launch_gmres_backsolve(ncols, m, K.d_H, K.d_g, K.d_y, ctx->stream));
     PP_CK(cudaMemsetAsync(K.w, 0, sizeof(double) * n, ctx->stream));
-    PP_CK(launch_update_norm2(n, K.V, n, j, K.d_y, K.w, ctx->d_scalar, ctx->d_partial, ctx->d_counter, ctx->stream));
+    PP_CK(launch_update_norm2(n, K.V, n, ncols, K.d_y, K.w, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
     if (prec) {
       PP_TRY(prec(K.w, K.t));
       PP_TRY(lincomb(ctx, n, x, {1.0, 1.0}, {x, K.t}));
     } else {
       PP_TRY(lincomb(ctx, n, x, {1.0, 1.0}, {x, K.w}));
     }
-    if (res <= tol || total >= maxit) {
-      done = true;
+    if (flag == 1.0 || flag == 2.0) {
+      status = PP_OK;
       break;
     }
+    if (total >= maxit) break;
     // restart from the true residual r = b - A x
-    const double* z = x;
-    if (prec) {
-      // x is already the preconditioned solution; A acts on it directly
-    }
-    PP_TRY(A(z, K.w));
+    PP_TRY(A(x, K.w));
     PP_TRY(lincomb(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
-    PP_TRY(host_norm(ctx, n, K.r, &beta));
-    if (beta <= tol) break;
   }
-  // the last synchronous copy above leaves the stream in order; report
   if (iters) *iters = total;
-  if (res_out) *res_out = 0.0;
-  return total >= maxit ? PP_ENOCONV : PP_OK;
+  if (res_out) *res_out = res;
+  return status;
 }
 
 struct StageView {
@@ -236,6 +215,10 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
   (void)d_rates;
   ctx->last_newton_iters = 0;
   ctx->last_gmres_iters = 0;
+  // chord Newton: all stages share a_ii = gamma, so the stored matrix of the previous
+  // stage (exact at its converged state) is the Newton matrix until contraction slows
+  const double* Jn = nullptr;
+  const double* An = nullptr;
   for (int step = 0; step < Nt; ++step) {
     const double t0 = step * dt;
     for (int i = 0; i < 3; ++i) {
@@ -252,34 +235,59 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
       double* Js = ctx->st_J + slot * mesh->ne * 4 * nb2(ctx);
       double* As = ctx->st_Ainv + slot * mesh->ne * nb2(ctx);
       double* us = ctx->st_u + slot * n;
-      double prev_res = INFINITY;
-      bool converged = false;
+      double prev_res = INFINITY, alpha = 1.0;
+      int backtracks = 0;
+      bool converged = false, refresh = (Jn == nullptr);
       for (int it = 0; it <= ctx->cfg.newton_maxit; ++it) {
         PP_TRY(lincomb(ctx, n, us, {1.0, ctx->A[i][i]}, {base, k[i]}));
         PP_CK(launch_residual(m, ctx->tb, ctx->ph, fr, us, r, ctx->stream));
         PP_CK(launch_stage_matvec(m, ctx->tb, nullptr, 1.0, 0.0, k[i], R, 0, ctx->stream));
         PP_TRY(lincomb(ctx, n, R, {1.0, -dt}, {R, r}));
-        double rn, mun;
-        PP_TRY(host_norm(ctx, n, R, &rn));
+        double rn2, mun;
+        PP_TRY(host_dot(ctx, n, R, R, &rn2));
+        double rn = std::sqrt(rn2);
+        // backtracking safeguard: a step that made the residual non-finite or larger is halved
+        if (it > 0 && (!std::isfinite(rn) || rn > prev_res) && backtracks < 8) {
+          alpha *= 0.5;
+          ++backtracks;
+          refresh = true;
+          PP_TRY(lincomb(ctx, n, k[i], {1.0, alpha}, {k[i], dk}));
+          continue;
+        }
+        if (!std::isfinite(rn)) return set_error(ctx, PP_ENAN, "non-finite stage residual");
+        if (it > 0 && rn > 0.25 * prev_res) refresh = true;  // slow chord contraction
+        alpha = 1.0;
         PP_CK(launch_stage_matvec(m, ctx->tb, nullptr, 1.0, 0.0, us, dk, 0, ctx->stream));
         PP_TRY(host_norm(ctx, n, dk, &mun));
-        // Jacobian and block-Jacobi inverse at the current stage state
-        PP_CK(launch_jacobian(m, ctx->tb, ctx->ph, fr, us, Js, ctx->stream));
-        PP_CK(launch_block_inverse(m, ctx->tb, Js, c, As, ctx->d_status, ctx->stream));
         const double tol = ctx->cfg.newton_tol * mun;
         if (rn <= tol || (it > 0 && rn <= 1e3 * tol && rn > 0.5 * prev_res)) {
           converged = true;
           break;
         }
         if (it == ctx->cfg.newton_maxit) break;
+        if (refresh) {
+          // Newton matrix at the current iterate (this stage's slot doubles as scratch)
+          PP_CK(launch_jacobian(m, ctx->tb, ctx->ph, fr, us, Js, ctx->stream));
+          PP_CK(launch_block_inverse(m, ctx->tb, Js, c, As, ctx->d_status, ctx->stream));
+          Jn = Js;
+          An = As;
+          refresh = false;
+        }
         prev_res = rn;
         int gits = 0;
-        StageView sv{Js, As, c};
+        StageView sv{Jn, An, c};
         int st = stage_solve(ctx, mesh, sv, 0, R, dk, ctx->cfg.gmres_rtol, 0.0, &gits);
         if (st != PP_OK && st != PP_ENOCONV) return st;
         ctx->last_gmres_iters += gits;
         PP_TRY(lincomb(ctx, n, k[i], {1.0, -1.0}, {k[i], dk}));
         ctx->last_newton_iters++;
+      }
+      if (converged) {
+        // exact Jacobian and preconditioner at the converged stage: the stored linearization
+        PP_CK(launch_jacobian(m, ctx->tb, ctx->ph, fr, us, Js, ctx->stream));
+        PP_CK(launch_block_inverse(m, ctx->tb, Js, c, As, ctx->d_status, ctx->stream));
+        Jn = Js;
+        An = As;
       }
       if (!converged) return set_error(ctx, PP_ENOCONV, "stage Newton did not converge");
       int status = 0;
@@ -336,6 +344,7 @@ int tangent_sweep(pp_ctx* ctx, const double* v, double* out) {
   double* v0 = work_vec(ctx, 15);
   PP_TRY(copy(ctx, n, v0, v));
   PP_TRY(copy(ctx, n, du, v));
+  ctx->last_gmres_tangent = 0;
   for (int step = 0; step < Nt; ++step) {
     for (int i = 0; i < 3; ++i) {
       StageView sv = stored_stage(ctx, step, i);
@@ -350,6 +359,7 @@ int tangent_sweep(pp_ctx* ctx, const double* v, double* out) {
       PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 0.0, dt, win, rhs, 0, ctx->stream));
       int gits = 0;
       PP_TRY(stage_solve(ctx, mesh, sv, 0, rhs, dk[i], ctx->cfg.lin_rtol, 0.0, &gits));
+      ctx->last_gmres_tangent += gits;
     }
     PP_TRY(lincomb(ctx, n, du, {1.0, ctx->b[0], ctx->b[1], ctx->b[2]}, {du, dk[0], dk[1], dk[2]}));
   }
@@ -377,6 +387,7 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
   const double w0 = withF ? weights[0] : 0.0, w1 = withF ? weights[1] : 0.0;
   std::vector<double> grad(n_mu, 0.0);
   PP_TRY(copy(ctx, n, lam, lam_Nt));
+  ctx->last_gmres_adjoint = 0;
   for (int step = Nt - 1; step >= 0; --step) {
     for (int i = 2; i >= 0; --i) {
       StageView sv = stored_stage(ctx, step, i);
@@ -406,6 +417,7 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
       }
       int gits = 0;
       PP_TRY(stage_solve(ctx, mesh, sv, 1, rhs, kap, ctx->cfg.lin_rtol, 0.0, &gits));
+      ctx->last_gmres_adjoint += gits;
       PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 0.0, dt, kap, y[i], 1, ctx->stream));
       if (withF && dFdmu) {
         // kappa_i . dr/ds and w . dQ/ds for the motion seeds s = theta, theta', h'

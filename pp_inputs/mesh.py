@@ -57,13 +57,29 @@ def _tag_faces(tris, ring_of_vertex, n_r):
     return ftag
 
 
-def ogrid(n_theta, n_r, seed=0, r_far=10.0, jitter=0.1, thickness=0.12):
-    """O-grid of 2*n_theta*n_r triangles around a symmetric 4-digit airfoil."""
-    beta = 2.0 * np.pi * np.arange(n_theta) / n_theta
+def _wall_points(n_theta, thickness, clustering):
+    """n_theta wall points, counter-clockwise from the trailing edge; 'arclength' spaces
+    them uniformly in arc length (LE hit exactly for even n_theta), 'cosine' uses
+    x = (1 + cos(beta))/2."""
+    if clustering == "cosine":
+        beta = 2.0 * np.pi * np.arange(n_theta) / n_theta
+    else:
+        bf = np.linspace(0.0, 2.0 * np.pi, 40001)
+        xf = 0.5 * (1.0 + np.cos(bf))
+        yf = _naca_half_thickness(xf, thickness) * np.where(np.sin(bf) >= 0, 1.0, -1.0)
+        sf = np.concatenate([[0.0], np.cumsum(np.hypot(np.diff(xf), np.diff(yf)))])
+        beta = np.interp(sf[-1] * np.arange(n_theta) / n_theta, sf, bf)
+        if n_theta % 2 == 0:
+            beta[n_theta // 2] = np.pi
     xw = 0.5 * (1.0 + np.cos(beta))
     yw = _naca_half_thickness(xw, thickness) * np.where(np.sin(beta) >= 0, 1.0, -1.0)
     yw[np.abs(np.sin(beta)) < 1e-14] = 0.0
-    wall = np.stack([xw, yw], 1)
+    return beta, np.stack([xw, yw], 1)
+
+
+def ogrid(n_theta, n_r, seed=0, r_far=10.0, jitter=0.1, thickness=0.12, clustering="arclength"):
+    """O-grid of 2*n_theta*n_r triangles around a symmetric 4-digit airfoil."""
+    beta, wall = _wall_points(n_theta, thickness, clustering)
     far = np.stack([0.5 + r_far * np.cos(beta), r_far * np.sin(beta)], 1)
     q = 1.0 + 4.0 / n_r
     s = (q ** np.arange(n_r + 1) - 1.0) / (q ** n_r - 1.0)
