@@ -153,9 +153,16 @@ def run_ours(args, rank, world, local_rank):
     weights = np.array([-1.0 / PHYS["T"], 0.0])   # F = J_E = -W/T
     newton = []
 
+    phase = {"primal": 0.0, "adjoint": 0.0}
+
     def step():
+        t0 = time.perf_counter()
         A.pp_primal_period(ctx, m, mu, u0, Nt, u_final=uN)
+        t1 = time.perf_counter()
         g = A.pp_adjoint_sweep(ctx, lamN, lam0, weights=weights, n_mu=len(mu))
+        t2 = time.perf_counter()
+        phase["primal"] += t1 - t0
+        phase["adjoint"] += t2 - t1
         u0.copy_(uN)
         return g
 
@@ -169,6 +176,7 @@ def run_ours(args, rank, world, local_rank):
         clk = ClockSampler(local_rank)
         clk.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        phase["primal"] = phase["adjoint"] = 0.0
         ev0.record(stream)
         for _ in range(args.steps):
             step()
@@ -181,6 +189,7 @@ def run_ours(args, rank, world, local_rank):
         iters = A.pp_sweep_counts(ctx)
         counts = A.pp_prof_counts()
         ms = ev0.elapsed_time(ev1) / args.steps
+        split = {k: 1e3 * v / args.steps for k, v in phase.items()}
 
         e2e = None
         if not args.no_e2e:
@@ -209,7 +218,7 @@ def run_ours(args, rank, world, local_rank):
     ms = float(tmax.item())
     A.pp_mesh_destroy(m)
     A.pp_destroy(ctx)
-    return dict(ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, kern_launches=launches_k, kern_ms=kern_ms,
+    return dict(ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, split=split, kern_launches=launches_k, kern_ms=kern_ms,
                 counts=counts, e2e=e2e)
 
 
@@ -306,6 +315,7 @@ def main():
         "gpu_launches": int(sum(res["counts"].values())),
         "launches_by_class": res["counts"],
         "last_step_iterations": res["iters"],
+        "ms_by_phase": res["split"],
     }
     if res["e2e"]:
         e = res["e2e"]

@@ -204,100 +204,118 @@ struct BlockOps {
   }
 };
 
+// One CTA (4 warps) per element; warp q handles block q of the element row (q = 0 the
+// diagonal block, q = 1..3 the face neighbours), so 4 independent column streams are in
+// flight per element; the 4 partial rows are combined in shared memory.
 template <int NB>
-__global__ void __launch_bounds__(MV_WARPS * 32)
+__global__ void __launch_bounds__(128)
     k_stage_matvec(DevMesh m, DevTables tb, const double* __restrict__ J, double alpha, double beta,
                    const double* __restrict__ x, double* __restrict__ y, int trans) {
   using Ops = BlockOps<NB>;
   constexpr int H = Ops::H;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * MV_WARPS + warp;
-  if (e >= m.ne) return;
-  const int Np = NB / 4;
   constexpr size_t nb2 = (size_t)NB * NB;
-  const double* xe = x + (size_t)e * NB;
-  double acc[H];
+  __shared__ double part[4][NB];
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x;
+  double s[H];
 #pragma unroll
-  for (int h = 0; h < H; ++h) {
-    acc[h] = 0.0;
-    const int r = lane + 32 * h;
-    if (alpha != 0.0 && r < NB) {
-      const int a = r / Np, i = r - a * Np;
-      double s = 0.0;
-      for (int j = 0; j < Np; ++j) s += tb.Mref[i * Np + j] * xe[a * Np + j];
-      acc[h] = alpha * m.detB[e] * s;
-    }
-  }
+  for (int h = 0; h < H; ++h) s[h] = 0.0;
   if (beta != 0.0) {
-    double s[H];
-#pragma unroll
-    for (int h = 0; h < H; ++h) s[h] = 0.0;
-    if (!trans) {
-      for (int slot = 0; slot < 4; ++slot) {
-        int src = e;
-        if (slot > 0) {
-          src = m.nbr[3 * e + slot - 1];
-          if (src < 0) continue;
-        }
-        double xr[H];
-        Ops::load(x + (size_t)src * NB, lane, xr);
-        Ops::mv(J + ((size_t)e * 4 + slot) * nb2, xr, lane, s);
-      }
+    const double* B = nullptr;
+    const double* xs = x + (size_t)e * NB;
+    if (q == 0) {
+      B = J + ((size_t)e * 4) * nb2;
     } else {
-      // (J^T x)_e = J_ee^T x_e + sum_f J_{e2,e}^T x_e2, J_{e2,e} = slot (1 + nbrface) of e2
-      const double* Bq[4];
-      double xq[4][H];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const double* src = xe;
-        Bq[q] = nullptr;
-        if (q == 0) {
-          Bq[q] = J + ((size_t)e * 4) * nb2;
-        } else {
-          const int e2 = m.nbr[3 * e + q - 1];
-          if (e2 >= 0) {
-            Bq[q] = J + ((size_t)e2 * 4 + 1 + m.nbrface[3 * e + q - 1]) * nb2;
-            src = x + (size_t)e2 * NB;
-          }
-        }
-        Ops::load(src, lane, xq[q]);
+      const int e2 = m.nbr[3 * e + q - 1];
+      if (e2 >= 0) {
+        B = trans ? J + ((size_t)e2 * 4 + 1 + m.nbrface[3 * e + q - 1]) * nb2 : J + ((size_t)e * 4 + q) * nb2;
+        xs = x + (size_t)e2 * NB;
       }
-      Ops::template mvt<4>(Bq, xq, lane, s);
     }
+    if (B) {
+      double xr[H];
+      Ops::load(xs, lane, xr);
+      if (!trans) {
+        Ops::mv(B, xr, lane, s);
+      } else {
+        const double* Bq[1] = {B};
+        double xq[1][H];
 #pragma unroll
-    for (int h = 0; h < H; ++h) acc[h] += beta * s[h];
+        for (int h = 0; h < H; ++h) xq[0][h] = xr[h];
+        Ops::template mvt<1>(Bq, xq, lane, s);
+      }
+    }
   }
 #pragma unroll
   for (int h = 0; h < H; ++h)
-    if (lane + 32 * h < NB) y[(size_t)e * NB + lane + 32 * h] = acc[h];
+    if (lane + 32 * h < NB) part[q][lane + 32 * h] = beta * s[h];
+  __syncthreads();
+  const int Np = NB / 4;
+  const double* xe = x + (size_t)e * NB;
+  for (int r = threadIdx.x; r < NB; r += 128) {
+    double acc = part[0][r] + part[1][r] + part[2][r] + part[3][r];
+    if (alpha != 0.0) {
+      const int a = r / Np, i = r - a * Np;
+      double mm = 0.0;
+      for (int jj = 0; jj < Np; ++jj) mm += tb.Mref[i * Np + jj] * xe[a * Np + jj];
+      acc += alpha * m.detB[e] * mm;
+    }
+    y[(size_t)e * NB + r] = acc;
+  }
 }
 
+// One CTA (4 warps) per element: normal product with the columns split over the warps,
+// transposed product with the outputs split over the warps (column r of A is row r of A^T).
 template <int NB>
-__global__ void __launch_bounds__(MV_WARPS * 32)
+__global__ void __launch_bounds__(128)
     k_block_apply(int ne, const double* __restrict__ Ainv, const double* __restrict__ x, double* __restrict__ y,
                   int trans) {
-  using Ops = BlockOps<NB>;
-  constexpr int H = Ops::H;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * MV_WARPS + warp;
-  if (e >= ne) return;
+  constexpr int H = (NB + 31) / 32;
+  constexpr int CW = (NB + 3) / 4;  // columns (or outputs) per warp
+  __shared__ double part[4][NB];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x;
   const double* A = Ainv + (size_t)e * NB * NB;
-  double acc[H];
+  const double* xe = x + (size_t)e * NB;
+  double xr[H];
 #pragma unroll
-  for (int h = 0; h < H; ++h) acc[h] = 0.0;
+  for (int h = 0; h < H; ++h) xr[h] = (lane + 32 * h < NB) ? xe[lane + 32 * h] : 0.0;
   if (!trans) {
-    double xr[H];
-    Ops::load(x + (size_t)e * NB, lane, xr);
-    Ops::mv(A, xr, lane, acc);
-  } else {
-    const double* Bq[1] = {A};
-    double xq[1][H];
-    Ops::load(x + (size_t)e * NB, lane, xq[0]);
-    Ops::template mvt<1>(Bq, xq, lane, acc);
-  }
+    double acc[H];
 #pragma unroll
-  for (int h = 0; h < H; ++h)
-    if (lane + 32 * h < NB) y[(size_t)e * NB + lane + 32 * h] = acc[h];
+    for (int h = 0; h < H; ++h) acc[h] = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < CW; ++cc) {
+      const int c = w * CW + cc;
+      if (c < NB) {
+        const double xc = __shfl_sync(0xffffffffu, xr[c >> 5], c & 31);
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          if (lane + 32 * h < NB) acc[h] += A[(size_t)c * NB + lane + 32 * h] * xc;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+      if (lane + 32 * h < NB) part[w][lane + 32 * h] = acc[h];
+  } else {
+#pragma unroll
+    for (int rr = 0; rr < CW; ++rr) {
+      const int r = w * CW + rr;
+      double p = 0.0;
+      if (r < NB) {
+        const double* col = A + (size_t)r * NB;
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          if (lane + 32 * h < NB) p += col[lane + 32 * h] * xr[h];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      if (r < NB && lane == 0) part[w][r] = p;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < NB; r += 128)
+    y[(size_t)e * NB + r] = trans ? part[r / CW][r] : part[0][r] + part[1][r] + part[2][r] + part[3][r];
 }
 
 __global__ void k_lincomb(int64_t n, double* y, int nterms, double c0, double c1, double c2, double c3,
@@ -333,21 +351,29 @@ __device__ __forceinline__ void block_partials(double* v, int kb, double* partia
   __syncthreads();
 }
 
-// last-block finalisation: out[j] = sum_b partial[b*k + j] in block order
-__device__ __forceinline__ void finish(int k, double* partial, unsigned* counter, double* out) {
+// Last-block finalisation: out[j] = sum_b partial[b*k + j].  Warp w reduces outputs
+// j = w, w + nwarps, ...; lanes stride over the block partials and a fixed xor
+// butterfly combines them, so the summation order is fixed (deterministic).
+// Returns true in the block that finished the reduction.
+__device__ __forceinline__ bool finish(int k, double* partial, unsigned* counter, double* out) {
   __shared__ bool last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < k; j += nw) {
     double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)partial)[(size_t)b * k + j];
-    out[j] = s;
+    for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(partial + (size_t)b * k + j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[j] = s;
   }
   if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
 }
 
 // dot products of w with vectors V_{j0..j0+kb-1} accumulated over this thread's indices
@@ -380,10 +406,70 @@ __device__ __forceinline__ void dots_any(int64_t n, const double* V, int64_t ldv
   }
 }
 
-// mode 0: out = V^T w;  mode 1: w -= V h, out = V^T w;  mode 2: w -= V h, out[0] = w.w;  mode 3: out[0] = V_0 . w
+struct GivensArgs {
+  int j, m;
+  const double* h1;
+  const double* h2;
+  double* H;
+  double* cs;
+  double* sn;
+  double* g;
+  double* stat;  // {res, tol, hn, 1/hn, beta, 1/beta, flag, j}
+};
+
+// Hessenberg column j = h1 + h2 and norm hn, previous rotations, new rotation, residual
+// estimate |g[j+1]| and stop flag (1 converged, 2 breakdown, 4 non-finite).  Loads are
+// staged in shared memory by the whole block; the rotation chain runs on one thread.
+__device__ __forceinline__ void givens_update(const GivensArgs& a, double nrm2) {
+  __shared__ double col[72], c_s[72], s_s[72];
+  const int j = a.j, m = a.m;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    col[i] = a.h1[i] + a.h2[i];
+    if (i < j) {
+      c_s[i] = a.cs[i];
+      s_s[i] = a.sn[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(fmax(nrm2, 0.0));
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t = c_s[i] * col[i] + s_s[i] * col[i + 1];
+      col[i + 1] = -s_s[i] * col[i] + c_s[i] * col[i + 1];
+      col[i] = t;
+    }
+    const double rr = hypot(col[j], col[j + 1]);
+    const double c = rr > 0.0 ? col[j] / rr : 1.0, s = rr > 0.0 ? col[j + 1] / rr : 0.0;
+    a.cs[j] = c;
+    a.sn[j] = s;
+    col[j] = rr;
+    col[j + 1] = 0.0;
+    const double gj = a.g[j];
+    a.g[j + 1] = -s * gj;
+    a.g[j] = c * gj;
+    const double res = fabs(s * gj);
+    a.stat[0] = res;
+    a.stat[2] = hn;
+    a.stat[3] = hn > 0.0 ? 1.0 / hn : 0.0;
+    double flag = 0.0;
+    if (res <= a.stat[1]) flag = 1.0;
+    if (hn == 0.0) flag = 2.0;
+    if (!isfinite(hn) || !isfinite(res)) flag = 4.0;
+    a.stat[6] = flag;
+    a.stat[7] = (double)j;
+  }
+  __syncthreads();
+  double* Hc = a.H + (size_t)j * (m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = col[i];
+}
+
+// mode 0: out = V^T w;  mode 1: w -= V h, out = V^T w;  mode 2: w -= V h, out[0] = w.w
+// (then the Givens update if gv.H != null);  mode 3: out[0] = V_0 . w
 __global__ void __launch_bounds__(RED_THREADS)
     k_krylov(int mode, int64_t n, const double* __restrict__ V, int64_t ldv, int k, const double* __restrict__ h,
-             double* __restrict__ w, double* __restrict__ out, double* __restrict__ partial, unsigned* counter) {
+             double* __restrict__ w, double* __restrict__ out, double* __restrict__ partial, unsigned* counter,
+             GivensArgs gv) {
   const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
   const int64_t i0 = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x;
   if (mode == 1 || mode == 2) {
@@ -395,7 +481,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   }
   if (mode == 2) {
     dots_batch<1>(n, w, 0, 0, 1, w, partial, 1);
-    finish(1, partial, counter, out);
+    if (finish(1, partial, counter, out) && gv.H) givens_update(gv, out[0]);
     return;
   }
   if (mode == 3) {
@@ -410,6 +496,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 // out[j] = sum_e per_elem[e*k + j], k <= 8
 __global__ void __launch_bounds__(RED_THREADS)
     k_colsum(int ne, int k, const double* __restrict__ pe, double* out, double* partial, unsigned* counter) {
+  // (finish() is used below; its return value is not needed here)
   double acc[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) acc[t] = 0.0;
@@ -508,7 +595,7 @@ cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const do
 cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const double* J, double alpha, double beta,
                                 const double* x, double* y, int trans, cudaStream_t st) {
   ProfScope ps(PP_K_STAGE_MATVEC, st);
-  const int g = (m.ne + MV_WARPS - 1) / MV_WARPS, b = MV_WARPS * 32;
+  const int g = m.ne, b = 128;
   switch (tb.nb) {
     case 12: k_stage_matvec<12><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
     case 24: k_stage_matvec<24><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
@@ -522,7 +609,7 @@ cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const dou
 cudaError_t launch_block_apply(const DevMesh& m, int nb, const double* Ainv, const double* x, double* y, int trans,
                                cudaStream_t st) {
   ProfScope ps(PP_K_BLOCK_APPLY, st);
-  const int g = (m.ne + MV_WARPS - 1) / MV_WARPS, b = MV_WARPS * 32;
+  const int g = m.ne, b = 128;
   switch (nb) {
     case 12: k_block_apply<12><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
     case 24: k_block_apply<24><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
@@ -578,21 +665,31 @@ cudaError_t launch_mdot(int64_t n, const double* V, int64_t ldv, int k, const do
                         double* partial, unsigned* counter, cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
   k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(0, n, V, ldv, k, nullptr, const_cast<double*>(w), out, partial,
-                                                  counter);
+                                                  counter, GivensArgs{});
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
                                double* out, double* partial, unsigned* counter, cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
-  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(1, n, V, ldv, k, h, w, out, partial, counter);
+  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(1, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_norm2(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
                                 double* out, double* partial, unsigned* counter, cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
-  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter);
+  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_norm2_givens(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
+                                       double* out, double* partial, unsigned* counter, int j, int m,
+                                       const double* h1, const double* h2, double* H, double* cs, double* sn,
+                                       double* g, double* stat, cudaStream_t st) {
+  ProfScope ps(PP_K_KRYLOV, st);
+  GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat};
+  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, gv);
   return cudaGetLastError();
 }
 
@@ -600,7 +697,7 @@ cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out,
                        unsigned* counter, cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
   k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(3, n, x, 0, 1, nullptr, const_cast<double*>(y), out, partial,
-                                                  counter);
+                                                  counter, GivensArgs{});
   return cudaGetLastError();
 }
 

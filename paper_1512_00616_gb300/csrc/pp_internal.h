@@ -157,6 +157,11 @@ cudaError_t launch_update_mdot(int64_t n, const double* V, int64_t ldv, int k, c
 // w -= V h[0:k]; then out[0] = w . w
 cudaError_t launch_update_norm2(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
                                 double* out, double* partial, unsigned* counter, cudaStream_t st);
+// w -= V h[0:k]; out[0] = w . w; then the GMRES Givens update of column j (see launch_gmres_givens)
+cudaError_t launch_update_norm2_givens(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
+                                       double* out, double* partial, unsigned* counter, int j, int m,
+                                       const double* h1, const double* h2, double* H, double* cs, double* sn,
+                                       double* g, double* stat, cudaStream_t st);
 // out[0] = x . y
 cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out, double* partial,
                        unsigned* counter, cudaStream_t st);

@@ -107,8 +107,8 @@ int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, 
       PP_TRY(A(z, K.w));
       PP_CK(launch_mdot(n, K.V, n, j + 1, K.w, d_h1, ctx->d_partial, ctx->d_counter, ctx->stream));
       PP_CK(launch_update_mdot(n, K.V, n, j + 1, d_h1, K.w, d_h2, ctx->d_partial, ctx->d_counter, ctx->stream));
-      PP_CK(launch_update_norm2(n, K.V, n, j + 1, d_h2, K.w, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
-      PP_CK(launch_gmres_givens(j, m, d_h1, d_h2, d_nrm, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
+      PP_CK(launch_update_norm2_givens(n, K.V, n, j + 1, d_h2, K.w, d_nrm, ctx->d_partial, ctx->d_counter, j, m, d_h1,
+                                       d_h2, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
       double* slot = K.h_h + 8 * (j % kRing);
       PP_CK(cudaMemcpyAsync(slot, K.d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
