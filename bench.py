@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     return ap.parse_args()
 
 
@@ -141,7 +142,8 @@ def run_ours(args, rank, world, local_rank):
     mu = config_mu(args.config)
     Nt = c["Nt"]
     stream = torch.cuda.Stream()
-    cfg = A.pp_config_default(p=c["p"], kin=c["kin"], T=PHYS["T"], device=local_rank, stream=stream.cuda_stream)
+    cfg = A.pp_config_default(p=c["p"], kin=c["kin"], T=PHYS["T"], device=local_rank, stream=stream.cuda_stream,
+                              precision=A.PP_PREC_MIXED if args.precision == "mixed" else A.PP_PREC_FP64)
     ctx = A.pp_create(cfg)
     m = A.pp_mesh_create(ctx, mesh.verts, mesh.tris, mesh.ftag)
     ne, npn, nu = A.pp_mesh_info(m)
@@ -306,8 +308,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload, "dof": res["nu"], "elements": res["ne"], "Nt": res["Nt"],
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": workload, "precision": args.precision, "dof": res["nu"], "elements": res["ne"], "Nt": res["Nt"],
                    "parallelism": f"replicas x{world}",
                    "l2": "working set (stored stage Jacobians, ~40 GB) far larger than L2; no flush needed"},
         "roofline": roof, "fp64_fma_peak_tflops_measured": fp64,

@@ -42,6 +42,13 @@ extern "C" {
 #define PP_ECUDA -6       /* a CUDA runtime call failed */
 #define PP_ESTATE -7      /* call needs a linearization that is not set */
 
+/* arithmetic of the stage linear solves */
+#define PP_PREC_FP64 0   /* FP64 block Jacobians, preconditioner and Krylov vectors throughout */
+#define PP_PREC_MIXED 1  /* FP32 copies of the block Jacobians and FP32 block-Jacobi inverses: the
+                            primal Newton steps are solved by FP32 GMRES (the Newton residual stays
+                            FP64); tangent / adjoint stage solves are FP64 flexible GMRES on the exact
+                            FP64 operator, preconditioned by a short FP32 GMRES */
+
 /* motion parametrizations (mu) -- Sec. 6.1 single-Fourier-mode motion */
 #define PP_KIN_HEAVE_PITCH 0 /* mu = (h0, theta0, phi): h = h0 sin(wt), theta = theta0 sin(wt + phi) */
 #define PP_KIN_FOURIER6 1    /* mu = (a1, b1, a2, al1, be1, al2): h = a1 sin wt + b1 cos wt + a2 sin 2wt,
@@ -77,6 +84,10 @@ typedef struct pp_config {
   double adj_tol;     /* absolute tolerance on ||lambda^(0)(x) - x||_2 */
   int adj_restart;
   int adj_maxit;
+  /* precision of the stage linear solves (PP_PREC_*) */
+  int precision;
+  int inner_maxit;    /* PP_PREC_MIXED: FP32 GMRES iterations per preconditioner application */
+  double inner_rtol;  /* PP_PREC_MIXED: relative tolerance of that inner solve */
 } pp_config;
 
 /* Fills *cfg with the paper's case (Sec. 6.1: gamma 1.4, Pr 0.72, Mach 0.2,

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libpp.so")
 
 PP_OK, PP_EINVAL, PP_ENOMEM, PP_ENOCONV, PP_ENAN, PP_EBREAKDOWN, PP_ECUDA, PP_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 PP_KIN_HEAVE_PITCH, PP_KIN_FOURIER6 = 0, 1
+PP_PREC_FP64, PP_PREC_MIXED = 0, 1
 STATUS_NAMES = {0: "PP_OK", -1: "PP_EINVAL", -2: "PP_ENOMEM", -3: "PP_ENOCONV", -4: "PP_ENAN",
                 -5: "PP_EBREAKDOWN", -6: "PP_ECUDA", -7: "PP_ESTATE"}
 
@@ -36,7 +37,8 @@ class pp_config(C.Structure):
                 ("gmres_rtol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
                 ("lin_rtol", C.c_double), ("nk_gmres_rtol", C.c_double), ("nk_restart", C.c_int),
                 ("nk_max_newton", C.c_int), ("nk_max_krylov", C.c_int), ("adj_tol", C.c_double),
-                ("adj_restart", C.c_int), ("adj_maxit", C.c_int)]
+                ("adj_restart", C.c_int), ("adj_maxit", C.c_int), ("precision", C.c_int),
+                ("inner_maxit", C.c_int), ("inner_rtol", C.c_double)]
 
 
 class pp_shoot_stats(C.Structure):

@@ -24,14 +24,18 @@ struct RefHost {
 };
 
 // Krylov workspace of one GMRES level (stage solves and the outer shooting /
-// periodic-adjoint solves each own one, because the latter call the former).
-struct Krylov {
+// periodic-adjoint solves each own one, because the latter call the former).  S is the
+// vector type; Hessenberg data and scalars are FP64.  Z (flexible GMRES only) keeps the
+// preconditioned directions.
+template <class S>
+struct KrylovT {
   int m = 0;
   int64_t n = 0;
-  double* V = nullptr;   // [m+1][n]
-  double* w = nullptr;   // [n]
-  double* t = nullptr;   // [n]
-  double* r = nullptr;   // [n]
+  S* V = nullptr;        // [m+1][n]
+  S* w = nullptr;        // [n]
+  S* t = nullptr;        // [n]
+  S* r = nullptr;        // [n]
+  S* Z = nullptr;        // [m][n] or null
   double* d_h = nullptr; // device: h1 [m+2] | h2 [m+2] | norm2 | y | H [(m+1) m] | cs | sn | g | stat [8]
   double* h_h = nullptr; // pinned ring of stat copies [kRing][8]
   double* d_y = nullptr; // [m+1]
@@ -42,6 +46,7 @@ struct Krylov {
   double* d_stat = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
+using Krylov = KrylovT<double>;
 constexpr int kRing = 4;
 
 // Motion quantities at one time and their derivatives w.r.t. mu.
@@ -79,7 +84,9 @@ struct pp_ctx {
   double* d_vec = nullptr;      // pool of work vectors
   int n_vec = 0;
   double* d_elem = nullptr;     // [ne*8] per-element partials
-  pp::Krylov kin, kout;         // inner (stage) and outer (shooting / periodic adjoint) GMRES
+  pp::Krylov kin, kout;         // stage-solve and outer (shooting / periodic adjoint) GMRES levels
+  pp::KrylovT<float> k32;       // inner FP32 level of the mixed-precision stage solves
+  float* d_vec32 = nullptr;     // FP32 work vectors [4][nu]
 
   // stored linearization (the last primal sweep)
   const pp_mesh* lin_mesh = nullptr;
@@ -90,6 +97,12 @@ struct pp_ctx {
   double* st_J = nullptr;       // [stages][ne*4*nb*nb]
   double* st_Ainv = nullptr;    // [stages][ne*nb*nb]
   double* st_u = nullptr;       // [stages][nu] stage states
+  double* st_JT = nullptr;      // [stages][ne*4*nb*nb] transposed block-columns (optional)
+  double* st_AinvT = nullptr;   // [stages][ne*nb*nb] transposed inverses (optional; FP64 mode)
+  float* st_J32 = nullptr;      // mixed mode: FP32 copies of J, J^T-columns and the inverses
+  float* st_JT32 = nullptr;
+  float* st_A32 = nullptr;
+  float* st_AT32 = nullptr;
   std::vector<double> lin_qoi_rates;  // [Nt*3][2]
   double lin_W = 0.0, lin_Jx = 0.0;
   int64_t last_newton_iters = 0;
@@ -119,11 +132,11 @@ int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_m
                      const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats);
 }  // namespace pp
 
-#define PP_CK(call)                                                                                  \
+#define PP_CK(...)                                                                                   \
   do {                                                                                               \
-    cudaError_t e_ = (call);                                                                         \
+    cudaError_t e_ = (__VA_ARGS__);                                                                  \
     if (e_ != cudaSuccess)                                                                           \
-      return pp::set_error(ctx, PP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+      return pp::set_error(ctx, PP_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
 #define PP_TRY(call)        \

@@ -213,18 +213,26 @@ int64_t mesh_nu(const pp_ctx* ctx, const pp_mesh* mesh) { return (int64_t)mesh->
 
 double* work_vec(pp_ctx* ctx, int i) { return ctx->d_vec + (size_t)i * ctx->ws_nu; }
 
-static int alloc_krylov(pp_ctx* ctx, Krylov& k, int m, int64_t n) {
-  if (k.V) {
-    cudaFree(k.V);
-    cudaFree(k.d_h);
-    cudaFreeHost(k.h_h);
-  }
+template <class S>
+static void free_krylov(KrylovT<S>& k) {
+  cudaFree(k.V);
+  cudaFree(k.Z);
+  cudaFree(k.d_h);
+  if (k.h_h) cudaFreeHost(k.h_h);
+  k.V = k.Z = nullptr;
+  k.d_h = k.h_h = nullptr;
+}
+
+template <class S>
+static int alloc_krylov(pp_ctx* ctx, KrylovT<S>& k, int m, int64_t n, bool flexible) {
+  free_krylov(k);
   k.m = m;
   k.n = n;
-  PP_CK(cudaMalloc(&k.V, sizeof(double) * (size_t)(m + 4) * n));
+  PP_CK(cudaMalloc(&k.V, sizeof(S) * (size_t)(m + 4) * n));
   k.w = k.V + (size_t)(m + 1) * n;
   k.t = k.w + n;
   k.r = k.t + n;
+  if (flexible) PP_CK(cudaMalloc(&k.Z, sizeof(S) * (size_t)m * n));
   const size_t nh = 2 * (m + 2) + 4 + (m + 2) + (size_t)(m + 1) * m + 3 * (m + 2) + 16;
   PP_CK(cudaMalloc(&k.d_h, sizeof(double) * nh));
   PP_CK(cudaMemset(k.d_h, 0, sizeof(double) * nh));
@@ -260,9 +268,16 @@ int ensure_workspace(pp_ctx* ctx, const pp_mesh* mesh) {
   }
   ctx->ws_ne = mesh->ne;
   ctx->ws_nu = nu;
-  PP_TRY(alloc_krylov(ctx, ctx->kin, ctx->cfg.gmres_restart, nu));
+  const bool mixed = ctx->cfg.precision == PP_PREC_MIXED;
+  PP_TRY(alloc_krylov(ctx, ctx->kin, ctx->cfg.gmres_restart, nu, mixed));
   int mo = ctx->cfg.nk_restart > ctx->cfg.adj_restart ? ctx->cfg.nk_restart : ctx->cfg.adj_restart;
-  PP_TRY(alloc_krylov(ctx, ctx->kout, mo, nu));
+  PP_TRY(alloc_krylov(ctx, ctx->kout, mo, nu, false));
+  if (mixed) {
+    int mi = ctx->cfg.inner_maxit > ctx->cfg.gmres_restart ? ctx->cfg.inner_maxit : ctx->cfg.gmres_restart;
+    PP_TRY(alloc_krylov(ctx, ctx->k32, mi, nu, false));
+    cudaFree(ctx->d_vec32);
+    PP_CK(cudaMalloc(&ctx->d_vec32, sizeof(float) * 4 * nu));
+  }
   ctx->lin_valid = false;
   return PP_OK;
 }
@@ -271,25 +286,50 @@ int ensure_store(pp_ctx* ctx, const pp_mesh* mesh, int Nt) {
   PP_TRY(ensure_workspace(ctx, mesh));
   const size_t stages = (size_t)Nt * 3;
   if (ctx->store_stages >= stages && ctx->lin_mesh == mesh) return PP_OK;
-  if (ctx->store_stages < stages || ctx->lin_mesh != mesh) {
-    cudaFree(ctx->st_J);
-    cudaFree(ctx->st_Ainv);
-    cudaFree(ctx->st_u);
-    ctx->st_J = ctx->st_Ainv = ctx->st_u = nullptr;
-    ctx->store_stages = 0;
-    const size_t nb2 = (size_t)ctx->tb.nb * ctx->tb.nb;
-    if (cudaMalloc(&ctx->st_J, sizeof(double) * stages * mesh->ne * 4 * nb2) != cudaSuccess ||
-        cudaMalloc(&ctx->st_Ainv, sizeof(double) * stages * mesh->ne * nb2) != cudaSuccess ||
-        cudaMalloc(&ctx->st_u, sizeof(double) * stages * mesh_nu(ctx, mesh)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(ctx->st_J);
-      cudaFree(ctx->st_Ainv);
-      cudaFree(ctx->st_u);
-      ctx->st_J = ctx->st_Ainv = ctx->st_u = nullptr;
-      return set_error(ctx, PP_ENOMEM, "linearization store does not fit in device memory");
+  auto release = [&]() {
+    for (double** p : {&ctx->st_J, &ctx->st_Ainv, &ctx->st_u, &ctx->st_JT, &ctx->st_AinvT}) {
+      cudaFree(*p);
+      *p = nullptr;
     }
-    ctx->store_stages = stages;
+    for (float** p : {&ctx->st_J32, &ctx->st_JT32, &ctx->st_A32, &ctx->st_AT32}) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    ctx->store_stages = 0;
+  };
+  release();
+  const bool mixed = ctx->cfg.precision == PP_PREC_MIXED;
+  const size_t nb2 = (size_t)ctx->tb.nb * ctx->tb.nb;
+  const size_t nJ = stages * mesh->ne * 4 * nb2, nA = stages * mesh->ne * nb2;
+  bool ok = cudaMalloc(&ctx->st_J, sizeof(double) * nJ) == cudaSuccess &&
+            cudaMalloc(&ctx->st_u, sizeof(double) * stages * mesh_nu(ctx, mesh)) == cudaSuccess;
+  if (ok && !mixed) ok = cudaMalloc(&ctx->st_Ainv, sizeof(double) * nA) == cudaSuccess;
+  if (ok && mixed)
+    ok = cudaMalloc(&ctx->st_J32, sizeof(float) * nJ) == cudaSuccess &&
+         cudaMalloc(&ctx->st_JT32, sizeof(float) * nJ) == cudaSuccess &&
+         cudaMalloc(&ctx->st_A32, sizeof(float) * nA) == cudaSuccess &&
+         cudaMalloc(&ctx->st_AT32, sizeof(float) * nA) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    release();
+    return set_error(ctx, PP_ENOMEM, "linearization store does not fit in device memory");
   }
+  // FP64 transposed copies let the adjoint stream row-major blocks with the normal
+  // kernels; they are kept only while at least 8 GB of device memory stay free
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  const size_t extra = sizeof(double) * (nJ + (mixed ? 0 : nA));
+  if (fr > extra + ((size_t)8 << 30)) {
+    bool okT = cudaMalloc(&ctx->st_JT, sizeof(double) * nJ) == cudaSuccess;
+    if (okT && !mixed) okT = cudaMalloc(&ctx->st_AinvT, sizeof(double) * nA) == cudaSuccess;
+    if (!okT) {
+      cudaGetLastError();
+      cudaFree(ctx->st_JT);
+      cudaFree(ctx->st_AinvT);
+      ctx->st_JT = ctx->st_AinvT = nullptr;
+    }
+  }
+  ctx->store_stages = stages;
   return PP_OK;
 }
 
@@ -327,13 +367,18 @@ void pp_config_default(pp_config* c) {
   c->adj_tol = 1e-10;
   c->adj_restart = 30;
   c->adj_maxit = 200;
+  c->precision = PP_PREC_FP64;
+  c->inner_maxit = 30;
+  c->inner_rtol = 1e-2;
 }
 
 int pp_create(const pp_config* cfg, pp_ctx** out) {
   if (!cfg || !out) return PP_EINVAL;
   if (cfg->p < 1 || cfg->p > kMaxP || cfg->gmres_restart < 1 || cfg->gmres_restart > 60 || cfg->nk_restart < 1 ||
       cfg->nk_restart > 60 || cfg->adj_restart < 1 || cfg->adj_restart > 60 || !(cfg->T > 0) || !(cfg->Re > 0) ||
-      !(cfg->Mach > 0) || (cfg->kin != PP_KIN_HEAVE_PITCH && cfg->kin != PP_KIN_FOURIER6))
+      !(cfg->Mach > 0) || (cfg->kin != PP_KIN_HEAVE_PITCH && cfg->kin != PP_KIN_FOURIER6) ||
+      (cfg->precision != PP_PREC_FP64 && cfg->precision != PP_PREC_MIXED) ||
+      (cfg->precision == PP_PREC_MIXED && (cfg->inner_maxit < 1 || cfg->inner_maxit > 60)))
     return PP_EINVAL;
   pp_ctx* ctx = new pp_ctx();
   ctx->cfg = *cfg;
@@ -416,17 +461,25 @@ int pp_destroy(pp_ctx* ctx) {
   cudaFree(ctx->d_J);
   cudaFree(ctx->d_Ainv);
   cudaFree(ctx->d_vec);
+  cudaFree(ctx->d_vec32);
   cudaFree(ctx->d_elem);
   for (Krylov* k : {&ctx->kin, &ctx->kout}) {
-    cudaFree(k->V);
-    cudaFree(k->d_h);
-    if (k->h_h) cudaFreeHost(k->h_h);
+    free_krylov(*k);
     for (int i = 0; i < kRing; ++i)
       if (k->ev[i]) cudaEventDestroy(k->ev[i]);
   }
+  free_krylov(ctx->k32);
+  for (int i = 0; i < kRing; ++i)
+    if (ctx->k32.ev[i]) cudaEventDestroy(ctx->k32.ev[i]);
   cudaFree(ctx->st_J);
   cudaFree(ctx->st_Ainv);
   cudaFree(ctx->st_u);
+  cudaFree(ctx->st_JT);
+  cudaFree(ctx->st_AinvT);
+  cudaFree(ctx->st_J32);
+  cudaFree(ctx->st_JT32);
+  cudaFree(ctx->st_A32);
+  cudaFree(ctx->st_AT32);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return PP_OK;

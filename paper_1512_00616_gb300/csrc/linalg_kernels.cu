@@ -1,17 +1,25 @@
-// Batched element-block linear algebra and Krylov vector kernels (FP64).
+// Batched element-block linear algebra and Krylov vector kernels, templated on the
+// storage/arithmetic type S (double for the FP64 path, float for the inner solves of
+// the mixed-precision path).
 //
-//  - k_block_inverse: A_e = detB_e Mref (x) I4 - c J_ee, the diagonal block of
-//    the DIRK stage matrix M - a_ii dt dr/du, inverted in shared memory by
-//    Gauss-Jordan elimination with partial pivoting.  The inverse is the
-//    block-Jacobi preconditioner of the stage solves; stored explicitly so that
-//    each application (normal for the primal and tangent sweeps, transposed for
-//    the adjoint sweep, Eq. uns-disc-adj-dirk2) is one dense block matvec
-//    streamed from HBM instead of two dependent triangular solves.
-//  - k_stage_matvec: y = alpha M x + beta J x (or beta J^T x) over the block-
-//    sparse element Jacobian (diagonal + 3 face-neighbour blocks).
-//  - Krylov vector kernels: fused multi-dot products with a deterministic
-//    two-level reduction (per-block partials, summed in block order by the
-//    last block to finish), used by the classical Gram-Schmidt (twice) Arnoldi.
+//  - k_block_inverse<S>: A_e = detB_e Mref (x) I4 - c J_ee (the diagonal block of the
+//    DIRK stage matrix M - a_ii dt dr/du, assembled in FP64) inverted in shared memory
+//    by Gauss-Jordan elimination with partial pivoting in precision S.  The inverse is
+//    the block-Jacobi preconditioner of the stage solves; it is stored explicitly (and
+//    transposed) so that every application, normal for the primal / tangent sweeps and
+//    transposed for the adjoint sweep (Eq. uns-disc-adj-dirk2), is one dense block
+//    matvec streamed from HBM.
+//  - k_stage_matvec<S>: y = alpha M x + beta J x (or J^T x) over the block-sparse
+//    element Jacobian (diagonal + 3 face-neighbour blocks).
+//  - k_transpose_blocks: per element, the transposed blocks of its block-column, so
+//    that J^T x runs through the same row-streaming kernel as J x.
+//  - k_krylov<S>: fused classical Gram-Schmidt (twice) steps with a deterministic
+//    two-level reduction (per-block partials, summed in a fixed order by the block that
+//    finishes last), and the GMRES Givens update fused into the norm kernel.
+//
+// GB300 note: its FP64 pipe issues ~2 DFMA per clock per SM, so FP64 block products are
+// ALU-bound (~21 us for the 4 x 40 x 40 x 2048 Jacobian product) before they are
+// HBM-bound; the same products in FP32 are bandwidth-bound.
 #include "pp_internal.h"
 #include "prof.h"
 #include "../../include/pp_prof.h"
@@ -21,15 +29,16 @@ namespace pp {
 namespace {
 
 constexpr int INV_THREADS = 256;
-constexpr int MV_WARPS = 4;
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
+constexpr int RED_BLOCKS = 152;  // one block per SM keeps the finishing reduction short
 
+// ------------------------------------------------------------------ block inverse
+template <class S>
 __global__ void __launch_bounds__(INV_THREADS)
-    k_block_inverse(DevMesh m, DevTables tb, const double* __restrict__ J, double c, double* __restrict__ Ainv,
-                    int* status) {
-  __shared__ double A[kMaxNb][kMaxNb + 1];
-  __shared__ double colk[kMaxNb];
+    k_block_inverse(DevMesh m, DevTables tb, const double* __restrict__ J, double c, S* __restrict__ Ainv,
+                    S* __restrict__ AinvT, int* status) {
+  __shared__ S A[kMaxNb][kMaxNb + 1];
+  __shared__ S colk[kMaxNb];
   __shared__ int piv[kMaxNb];
   __shared__ int s_p;
   const int e = blockIdx.x, tid = threadIdx.x;
@@ -41,15 +50,15 @@ __global__ void __launch_bounds__(INV_THREADS)
     int col = ent / nb, row = ent - col * nb;
     int a = row / Np, i = row - a * Np, b = col / Np, j = col - b * Np;
     double mass = (a == b) ? detB * tb.Mref[i * Np + j] : 0.0;
-    A[row][col] = mass - c * Je[ent];
+    A[row][col] = S(mass - c * Je[ent]);
   }
   __syncthreads();
   for (int k = 0; k < nb; ++k) {
     if (tid < 32) {
-      double best = -1.0;
+      S best = S(-1);
       int bi = k;
       for (int i = k + tid; i < nb; i += 32) {
-        double v = fabs(A[i][k]);
+        S v = fabs(A[i][k]);
         if (v > best) {
           best = v;
           bi = i;
@@ -57,7 +66,7 @@ __global__ void __launch_bounds__(INV_THREADS)
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        S ob = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
@@ -67,21 +76,21 @@ __global__ void __launch_bounds__(INV_THREADS)
       if (tid == 0) {
         s_p = bi;
         piv[k] = bi;
-        if (!(best > 0.0) || !isfinite(best)) atomicOr(status, 1);
+        if (!(best > S(0)) || !isfinite((double)best)) atomicOr(status, 1);
       }
     }
     __syncthreads();
     const int p = s_p;
     if (p != k)
       for (int j = tid; j < nb; j += INV_THREADS) {
-        double t = A[k][j];
+        S t = A[k][j];
         A[k][j] = A[p][j];
         A[p][j] = t;
       }
     __syncthreads();
-    const double pinv = 1.0 / A[k][k];
+    const S pinv = S(1) / A[k][k];
     __syncthreads();
-    if (tid == 0) A[k][k] = 1.0;
+    if (tid == 0) A[k][k] = S(1);
     __syncthreads();
     for (int j = tid; j < nb; j += INV_THREADS) A[k][j] *= pinv;
     for (int i = tid; i < nb; i += INV_THREADS) colk[i] = A[i][k];
@@ -89,8 +98,8 @@ __global__ void __launch_bounds__(INV_THREADS)
     for (int ent = tid; ent < nb * nb; ent += INV_THREADS) {
       int i = ent / nb, j = ent - i * nb;
       if (i == k) continue;
-      double f = colk[i];
-      double v = (j == k) ? 0.0 : A[i][j];
+      S f = colk[i];
+      S v = (j == k) ? S(0) : A[i][j];
       A[i][j] = v - f * A[k][j];
     }
     __syncthreads();
@@ -100,45 +109,48 @@ __global__ void __launch_bounds__(INV_THREADS)
     for (int k = nb - 1; k >= 0; --k) {
       int p = piv[k];
       if (p != k) {
-        double t = A[i][k];
+        S t = A[i][k];
         A[i][k] = A[i][p];
         A[i][p] = t;
       }
     }
   }
   __syncthreads();
-  double* out = Ainv + (size_t)e * nb2;
+  S* out = Ainv + (size_t)e * nb2;
+  S* outT = AinvT ? AinvT + (size_t)e * nb2 : nullptr;
   for (int ent = tid; ent < nb * nb; ent += INV_THREADS) {
     int col = ent / nb, row = ent - col * nb;
     out[ent] = A[row][col];
+    if (outT) outT[ent] = A[col][row];
   }
 }
 
-// Warp reduce-scatter of KB (power of two, <= 32) per-lane values: afterwards lane l
-// holds the warp sum of value (l >> (5 - log2 KB)) in v[0] (31 shuffles for KB = 32).
-template <int CNT, int O>
-__device__ __forceinline__ void rs_step(double* v, int lane) {
+// ------------------------------------------------------------------ warp reduce-scatter
+template <int CNT, int O, class T>
+__device__ __forceinline__ void rs_step(T* v, int lane) {
   if constexpr (O > 0) {
     if constexpr (CNT > 1) {
       constexpr int half = CNT / 2;
       const bool upper = (lane & O) != 0;
 #pragma unroll
       for (int t = 0; t < half; ++t) {
-        const double send = upper ? v[t] : v[t + half];
-        const double keep = upper ? v[t + half] : v[t];
+        const T send = upper ? v[t] : v[t + half];
+        const T keep = upper ? v[t + half] : v[t];
         v[t] = keep + __shfl_xor_sync(0xffffffffu, send, O);
       }
-      rs_step<half, O / 2>(v, lane);
+      rs_step<half, O / 2, T>(v, lane);
     } else {
       v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
-      rs_step<1, O / 2>(v, lane);
+      rs_step<1, O / 2, T>(v, lane);
     }
   }
 }
 
-template <int KB>
-__device__ __forceinline__ void warp_reduce_scatter(double* v, int lane) {
-  rs_step<KB, 16>(v, lane);
+// Warp reduce-scatter of KB (power of two, <= 32) per-lane values: afterwards lane l
+// holds the warp sum of value (l >> (5 - log2 KB)) in v[0] (31 shuffles for KB = 32).
+template <int KB, class T>
+__device__ __forceinline__ void warp_reduce_scatter(T* v, int lane) {
+  rs_step<KB, 16, T>(v, lane);
 }
 
 template <int KB>
@@ -146,51 +158,51 @@ struct ILog2 {
   static constexpr int value = KB >= 32 ? 5 : KB >= 16 ? 4 : KB >= 8 ? 3 : KB >= 4 ? 2 : KB >= 2 ? 1 : 0;
 };
 
-// Warp-per-element block products with compile-time block size NB = 4 Np.
-// Normal: lanes over rows, inputs broadcast by shuffles, columns streamed (column-major,
-// coalesced).  Transposed: output r is the dot product of the contiguous column r with
-// the input, so lanes run over the column and a reduce-scatter across the warp delivers
-// 32 outputs at a time.
-template <int NB>
+// ------------------------------------------------------------------ block products
+// Warp-per-block products with compile-time block size NB = 4 Np.  Normal: lanes over
+// rows, the input values read with warp-uniform loads into registers, columns streamed
+// (column-major, coalesced).  Transposed: output r is the dot product of the contiguous
+// column r with the input, so lanes run over the column and a reduce-scatter across the
+// warp delivers 32 outputs at a time.
+template <int NB, class S>
 struct BlockOps {
   static constexpr int H = (NB + 31) / 32;
 
-  __device__ static __forceinline__ void load(const double* x, int lane, double xr[H]) {
+  __device__ static __forceinline__ void load(const S* x, int lane, S xr[H]) {
 #pragma unroll
-    for (int h = 0; h < H; ++h) xr[h] = (lane + 32 * h < NB) ? x[lane + 32 * h] : 0.0;
+    for (int h = 0; h < H; ++h) xr[h] = (lane + 32 * h < NB) ? x[lane + 32 * h] : S(0);
   }
 
-  // acc[h] += (B x)[lane + 32h], B column-major NB x NB
-  __device__ static __forceinline__ void mv(const double* __restrict__ B, const double xr[H], int lane,
-                                            double acc[H]) {
-#pragma unroll 8
+  __device__ static __forceinline__ void mv_x(const S* __restrict__ B, const S* __restrict__ x, int lane,
+                                              S acc[H]) {
+    S xc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) xc[c] = __ldg(x + c);
+#pragma unroll
     for (int c = 0; c < NB; ++c) {
-      const double xc = __shfl_sync(0xffffffffu, xr[c >> 5], c & 31);
 #pragma unroll
       for (int h = 0; h < H; ++h)
-        if (lane + 32 * h < NB) acc[h] += B[(size_t)c * NB + lane + 32 * h] * xc;
+        if (lane + 32 * h < NB) acc[h] += __ldg(B + (size_t)c * NB + lane + 32 * h) * xc[c];
     }
   }
 
-  // out[h] = sum_q (B_q^T x_q)[lane + 32h] over NQ blocks (null blocks skipped)
   template <int NQ>
-  __device__ static __forceinline__ void mvt(const double* const (&Bq)[NQ], const double (&xq)[NQ][H], int lane,
-                                             double out[H]) {
+  __device__ static __forceinline__ void mvt(const S* const (&Bq)[NQ], const S (&xq)[NQ][H], int lane, S out[H]) {
 #pragma unroll
     for (int b = 0; b < H; ++b) {
       constexpr int KB = 32;
-      double acc[KB];
+      S acc[KB];
 #pragma unroll
-      for (int t = 0; t < KB; ++t) acc[t] = 0.0;
+      for (int t = 0; t < KB; ++t) acc[t] = S(0);
       const int r0 = 32 * b;
 #pragma unroll
       for (int t = 0; t < KB; ++t) {
         if (r0 + t < NB) {
-          double part = 0.0;
+          S part = S(0);
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             if (!Bq[q]) continue;
-            const double* col = Bq[q] + (size_t)(r0 + t) * NB;
+            const S* col = Bq[q] + (size_t)(r0 + t) * NB;
 #pragma unroll
             for (int h = 0; h < H; ++h)
               if (lane + 32 * h < NB) part += col[lane + 32 * h] * xq[q][h];
@@ -198,48 +210,47 @@ struct BlockOps {
           acc[t] = part;
         }
       }
-      warp_reduce_scatter<KB>(acc, lane);
+      warp_reduce_scatter<KB, S>(acc, lane);
       out[b] = acc[0];
     }
   }
 };
 
 // One CTA (4 warps) per element; warp q handles block q of the element row (q = 0 the
-// diagonal block, q = 1..3 the face neighbours), so 4 independent column streams are in
-// flight per element; the 4 partial rows are combined in shared memory.
-template <int NB>
+// diagonal block, q = 1..3 the face neighbours); the 4 partial rows meet in shared memory.
+template <int NB, bool TRANS, class S>
 __global__ void __launch_bounds__(128)
-    k_stage_matvec(DevMesh m, DevTables tb, const double* __restrict__ J, double alpha, double beta,
-                   const double* __restrict__ x, double* __restrict__ y, int trans) {
-  using Ops = BlockOps<NB>;
+    k_stage_matvec(DevMesh m, DevTables tb, const S* __restrict__ J, double alpha, double beta,
+                   const S* __restrict__ x, S* __restrict__ y) {
+  using Ops = BlockOps<NB, S>;
   constexpr int H = Ops::H;
   constexpr size_t nb2 = (size_t)NB * NB;
-  __shared__ double part[4][NB];
+  __shared__ S part[4][NB];
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x;
-  double s[H];
+  S s[H];
 #pragma unroll
-  for (int h = 0; h < H; ++h) s[h] = 0.0;
+  for (int h = 0; h < H; ++h) s[h] = S(0);
   if (beta != 0.0) {
-    const double* B = nullptr;
-    const double* xs = x + (size_t)e * NB;
+    const S* B = nullptr;
+    const S* xs = x + (size_t)e * NB;
     if (q == 0) {
       B = J + ((size_t)e * 4) * nb2;
     } else {
       const int e2 = m.nbr[3 * e + q - 1];
       if (e2 >= 0) {
-        B = trans ? J + ((size_t)e2 * 4 + 1 + m.nbrface[3 * e + q - 1]) * nb2 : J + ((size_t)e * 4 + q) * nb2;
+        B = TRANS ? J + ((size_t)e2 * 4 + 1 + m.nbrface[3 * e + q - 1]) * nb2 : J + ((size_t)e * 4 + q) * nb2;
         xs = x + (size_t)e2 * NB;
       }
     }
     if (B) {
-      double xr[H];
-      Ops::load(xs, lane, xr);
-      if (!trans) {
-        Ops::mv(B, xr, lane, s);
+      if constexpr (!TRANS) {
+        Ops::mv_x(B, xs, lane, s);
       } else {
-        const double* Bq[1] = {B};
-        double xq[1][H];
+        S xr[H];
+        Ops::load(xs, lane, xr);
+        const S* Bq[1] = {B};
+        S xq[1][H];
 #pragma unroll
         for (int h = 0; h < H; ++h) xq[0][h] = xr[h];
         Ops::template mvt<1>(Bq, xq, lane, s);
@@ -248,62 +259,61 @@ __global__ void __launch_bounds__(128)
   }
 #pragma unroll
   for (int h = 0; h < H; ++h)
-    if (lane + 32 * h < NB) part[q][lane + 32 * h] = beta * s[h];
+    if (lane + 32 * h < NB) part[q][lane + 32 * h] = S(beta) * s[h];
   __syncthreads();
   const int Np = NB / 4;
-  const double* xe = x + (size_t)e * NB;
+  const S* xe = x + (size_t)e * NB;
   for (int r = threadIdx.x; r < NB; r += 128) {
-    double acc = part[0][r] + part[1][r] + part[2][r] + part[3][r];
+    S acc = part[0][r] + part[1][r] + part[2][r] + part[3][r];
     if (alpha != 0.0) {
       const int a = r / Np, i = r - a * Np;
-      double mm = 0.0;
-      for (int jj = 0; jj < Np; ++jj) mm += tb.Mref[i * Np + jj] * xe[a * Np + jj];
-      acc += alpha * m.detB[e] * mm;
+      S mm = S(0);
+      for (int jj = 0; jj < Np; ++jj) mm += S(tb.Mref[i * Np + jj]) * xe[a * Np + jj];
+      acc += S(alpha * m.detB[e]) * mm;
     }
     y[(size_t)e * NB + r] = acc;
   }
 }
 
 // One CTA (4 warps) per element: normal product with the columns split over the warps,
-// transposed product with the outputs split over the warps (column r of A is row r of A^T).
-template <int NB>
+// transposed product with the outputs split over the warps.
+template <int NB, bool TRANS, class S>
 __global__ void __launch_bounds__(128)
-    k_block_apply(int ne, const double* __restrict__ Ainv, const double* __restrict__ x, double* __restrict__ y,
-                  int trans) {
+    k_block_apply(int ne, const S* __restrict__ Ainv, const S* __restrict__ x, S* __restrict__ y) {
   constexpr int H = (NB + 31) / 32;
   constexpr int CW = (NB + 3) / 4;  // columns (or outputs) per warp
-  __shared__ double part[4][NB];
+  __shared__ S part[4][NB];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x;
-  const double* A = Ainv + (size_t)e * NB * NB;
-  const double* xe = x + (size_t)e * NB;
-  double xr[H];
+  const S* A = Ainv + (size_t)e * NB * NB;
+  const S* xe = x + (size_t)e * NB;
+  if constexpr (!TRANS) {
+    S acc[H];
 #pragma unroll
-  for (int h = 0; h < H; ++h) xr[h] = (lane + 32 * h < NB) ? xe[lane + 32 * h] : 0.0;
-  if (!trans) {
-    double acc[H];
-#pragma unroll
-    for (int h = 0; h < H; ++h) acc[h] = 0.0;
+    for (int h = 0; h < H; ++h) acc[h] = S(0);
 #pragma unroll
     for (int cc = 0; cc < CW; ++cc) {
       const int c = w * CW + cc;
       if (c < NB) {
-        const double xc = __shfl_sync(0xffffffffu, xr[c >> 5], c & 31);
+        const S xc = __ldg(xe + c);
 #pragma unroll
         for (int h = 0; h < H; ++h)
-          if (lane + 32 * h < NB) acc[h] += A[(size_t)c * NB + lane + 32 * h] * xc;
+          if (lane + 32 * h < NB) acc[h] += __ldg(A + (size_t)c * NB + lane + 32 * h) * xc;
       }
     }
 #pragma unroll
     for (int h = 0; h < H; ++h)
       if (lane + 32 * h < NB) part[w][lane + 32 * h] = acc[h];
   } else {
+    S xr[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) xr[h] = (lane + 32 * h < NB) ? xe[lane + 32 * h] : S(0);
 #pragma unroll
     for (int rr = 0; rr < CW; ++rr) {
       const int r = w * CW + rr;
-      double p = 0.0;
+      S p = S(0);
       if (r < NB) {
-        const double* col = A + (size_t)r * NB;
+        const S* col = A + (size_t)r * NB;
 #pragma unroll
         for (int h = 0; h < H; ++h)
           if (lane + 32 * h < NB) p += col[lane + 32 * h] * xr[h];
@@ -315,33 +325,78 @@ __global__ void __launch_bounds__(128)
   }
   __syncthreads();
   for (int r = threadIdx.x; r < NB; r += 128)
-    y[(size_t)e * NB + r] = trans ? part[r / CW][r] : part[0][r] + part[1][r] + part[2][r] + part[3][r];
+    y[(size_t)e * NB + r] = TRANS ? part[r / CW][r] : part[0][r] + part[1][r] + part[2][r] + part[3][r];
 }
 
-__global__ void k_lincomb(int64_t n, double* y, int nterms, double c0, double c1, double c2, double c3,
-                          const double* x0, const double* x1, const double* x2, const double* x3) {
+// JT[e][q] = (block of J in block-row src_q(e), block-column e)^T, column-major, so that
+// J^T x is the same block-row product as J x with JT in place of J.  q = 0: J_ee;
+// q = 1+f: J_{e2,e} = J[e2][1 + nbrface(e,f)], e2 = nbr(e,f); zero on boundary faces.
+// One CTA per (element, slot), tile staged in shared memory; the output type may be
+// narrower than the input (FP64 -> FP32 copy for the mixed-precision path).
+template <class Si, class So>
+__global__ void __launch_bounds__(256)
+    k_transpose_blocks(DevMesh m, int nb, const Si* __restrict__ J, So* __restrict__ JT) {
+  __shared__ Si T[kMaxNb][kMaxNb + 1];
+  const int e = blockIdx.x >> 2, q = blockIdx.x & 3;
+  const size_t nb2 = (size_t)nb * nb;
+  So* dst = JT + ((size_t)e * 4 + q) * nb2;
+  const Si* src = nullptr;
+  if (q == 0) {
+    src = J + ((size_t)e * 4) * nb2;
+  } else {
+    const int e2 = m.nbr[3 * e + q - 1];
+    if (e2 >= 0) src = J + ((size_t)e2 * 4 + 1 + m.nbrface[3 * e + q - 1]) * nb2;
+  }
+  if (!src) {
+    for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) dst[i] = So(0);
+    return;
+  }
+  for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) {
+    const int col = i / nb, row = i - col * nb;
+    T[row][col] = src[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) {
+    const int col = i / nb, row = i - col * nb;  // (row, col) of the transpose
+    dst[i] = So(T[col][row]);
+  }
+}
+
+// ------------------------------------------------------------------ vector kernels
+template <class S>
+__global__ void k_lincomb(int64_t n, S* y, int nterms, double c0, double c1, double c2, double c3, const S* x0,
+                          const S* x1, const S* x2, const S* x3) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = c0 * x0[i];
-    if (nterms > 1) s += c1 * x1[i];
-    if (nterms > 2) s += c2 * x2[i];
-    if (nterms > 3) s += c3 * x3[i];
+    S s = S(c0) * x0[i];
+    if (nterms > 1) s += S(c1) * x1[i];
+    if (nterms > 2) s += S(c2) * x2[i];
+    if (nterms > 3) s += S(c3) * x3[i];
     y[i] = s;
   }
 }
 
-__global__ void k_scale(int64_t n, double* y, double a, const double* x) {
+template <class S>
+__global__ void k_scale_dev(int64_t n, S* y, const double* a, const S* x) {
+  const S s = S(a[0]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i];
+    y[i] = s * x[i];
 }
 
+template <class Si, class So>
+__global__ void k_cast(int64_t n, So* y, const Si* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = So(x[i]);
+}
+
+// ------------------------------------------------------------------ reductions
 // block partial sums of KB per-thread values -> partial[blockIdx*ld + j0 + t], t < kb
-template <int KB>
-__device__ __forceinline__ void block_partials(double* v, int kb, double* partial, int ld, int j0) {
+template <int KB, class S>
+__device__ __forceinline__ void block_partials(S* v, int kb, double* partial, int ld, int j0) {
   __shared__ double red[32][RED_THREADS / 32 + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  warp_reduce_scatter<KB>(v, lane);
+  warp_reduce_scatter<KB, S>(v, lane);
   constexpr int sh = 5 - ILog2<KB>::value;
-  if ((lane & ((1 << sh) - 1)) == 0) red[lane >> sh][warp] = v[0];
+  if ((lane & ((1 << sh) - 1)) == 0) red[lane >> sh][warp] = (double)v[0];
   __syncthreads();
   if (threadIdx.x < kb) {
     double s = 0.0;
@@ -377,32 +432,32 @@ __device__ __forceinline__ bool finish(int k, double* partial, unsigned* counter
 }
 
 // dot products of w with vectors V_{j0..j0+kb-1} accumulated over this thread's indices
-template <int KB>
-__device__ __forceinline__ void dots_batch(int64_t n, const double* __restrict__ V, int64_t ldv, int j0, int kb,
-                                           const double* w, double* partial, int ld) {
-  double acc[KB];
+template <int KB, class S>
+__device__ __forceinline__ void dots_batch(int64_t n, const S* __restrict__ V, int64_t ldv, int j0, int kb,
+                                           const S* w, double* partial, int ld) {
+  S acc[KB];
 #pragma unroll
-  for (int t = 0; t < KB; ++t) acc[t] = 0.0;
+  for (int t = 0; t < KB; ++t) acc[t] = S(0);
   const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
   for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += stride) {
-    const double wi = w[i];
+    const S wi = w[i];
 #pragma unroll
     for (int t = 0; t < KB; ++t)
       if (t < kb) acc[t] += V[(int64_t)(j0 + t) * ldv + i] * wi;
   }
-  block_partials<KB>(acc, kb, partial, ld, j0);
+  block_partials<KB, S>(acc, kb, partial, ld, j0);
 }
 
-__device__ __forceinline__ void dots_any(int64_t n, const double* V, int64_t ldv, int k, const double* w,
-                                         double* partial) {
+template <class S>
+__device__ __forceinline__ void dots_any(int64_t n, const S* V, int64_t ldv, int k, const S* w, double* partial) {
   for (int j0 = 0; j0 < k; j0 += 32) {
     const int kb = min(32, k - j0);
-    if (kb > 16) dots_batch<32>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 8) dots_batch<16>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 4) dots_batch<8>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 2) dots_batch<4>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 1) dots_batch<2>(n, V, ldv, j0, kb, w, partial, k);
-    else dots_batch<1>(n, V, ldv, j0, kb, w, partial, k);
+    if (kb > 16) dots_batch<32, S>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 8) dots_batch<16, S>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 4) dots_batch<8, S>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 2) dots_batch<4, S>(n, V, ldv, j0, kb, w, partial, k);
+    else if (kb > 1) dots_batch<2, S>(n, V, ldv, j0, kb, w, partial, k);
+    else dots_batch<1, S>(n, V, ldv, j0, kb, w, partial, k);
   }
 }
 
@@ -466,37 +521,37 @@ __device__ __forceinline__ void givens_update(const GivensArgs& a, double nrm2) 
 
 // mode 0: out = V^T w;  mode 1: w -= V h, out = V^T w;  mode 2: w -= V h, out[0] = w.w
 // (then the Givens update if gv.H != null);  mode 3: out[0] = V_0 . w
+template <class S>
 __global__ void __launch_bounds__(RED_THREADS)
-    k_krylov(int mode, int64_t n, const double* __restrict__ V, int64_t ldv, int k, const double* __restrict__ h,
-             double* __restrict__ w, double* __restrict__ out, double* __restrict__ partial, unsigned* counter,
+    k_krylov(int mode, int64_t n, const S* __restrict__ V, int64_t ldv, int k, const double* __restrict__ h,
+             S* __restrict__ w, double* __restrict__ out, double* __restrict__ partial, unsigned* counter,
              GivensArgs gv) {
   const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
   const int64_t i0 = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x;
   if (mode == 1 || mode == 2) {
     for (int64_t i = i0; i < n; i += stride) {
-      double s = w[i];
-      for (int j = 0; j < k; ++j) s -= h[j] * V[j * ldv + i];
+      S s = w[i];
+      for (int j = 0; j < k; ++j) s -= S(h[j]) * V[j * ldv + i];
       w[i] = s;
     }
   }
   if (mode == 2) {
-    dots_batch<1>(n, w, 0, 0, 1, w, partial, 1);
+    dots_batch<1, S>(n, w, 0, 0, 1, w, partial, 1);
     if (finish(1, partial, counter, out) && gv.H) givens_update(gv, out[0]);
     return;
   }
   if (mode == 3) {
-    dots_batch<1>(n, V, 0, 0, 1, w, partial, 1);
+    dots_batch<1, S>(n, V, 0, 0, 1, w, partial, 1);
     finish(1, partial, counter, out);
     return;
   }
-  dots_any(n, V, ldv, k, w, partial);
+  dots_any<S>(n, V, ldv, k, w, partial);
   finish(k, partial, counter, out);
 }
 
 // out[j] = sum_e per_elem[e*k + j], k <= 8
 __global__ void __launch_bounds__(RED_THREADS)
     k_colsum(int ne, int k, const double* __restrict__ pe, double* out, double* partial, unsigned* counter) {
-  // (finish() is used below; its return value is not needed here)
   double acc[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) acc[t] = 0.0;
@@ -504,14 +559,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 #pragma unroll
     for (int t = 0; t < 8; ++t)
       if (t < k) acc[t] += pe[(size_t)e * k + t];
-  block_partials<8>(acc, k, partial, k, 0);
+  block_partials<8, double>(acc, k, partial, k, 0);
   finish(k, partial, counter, out);
-}
-
-__global__ void k_scale_dev(int64_t n, double* y, const double* a, const double* x) {
-  const double s = a[0];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = s * x[i];
 }
 
 // GMRES bookkeeping on the device (one thread): stat = {res, tol, hn, inv_hn, beta, inv_beta, flag, j}
@@ -527,37 +576,6 @@ __global__ void k_gmres_init(const double* bb, double rtol, double atol, int fir
   stat[6] = (beta <= stat[1]) ? 1.0 : 0.0;
   if (!isfinite(beta)) stat[6] = 4.0;
   stat[7] = -1.0;
-}
-
-__global__ void k_gmres_givens(int j, int m, const double* h1, const double* h2, const double* nrm2, double* H,
-                               double* cs, double* sn, double* g, double* stat) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  const double hn = sqrt(fmax(nrm2[0], 0.0));
-  col[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
-  }
-  const double rr = hypot(col[j], col[j + 1]);
-  cs[j] = rr > 0.0 ? col[j] / rr : 1.0;
-  sn[j] = rr > 0.0 ? col[j + 1] / rr : 0.0;
-  col[j] = rr;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  const double res = fabs(g[j + 1]);
-  stat[0] = res;
-  stat[2] = hn;
-  stat[3] = hn > 0.0 ? 1.0 / hn : 0.0;
-  double flag = 0.0;
-  if (res <= stat[1]) flag = 1.0;
-  if (hn == 0.0) flag = 2.0;
-  if (!isfinite(hn) || !isfinite(res)) flag = 4.0;
-  stat[6] = flag;
-  stat[7] = (double)j;
 }
 
 // y = -(H^{-1} g) on the leading ncols x ncols triangle (negated for the fused update kernel)
@@ -585,53 +603,83 @@ int red_blocks(int64_t n) {
 
 int reduction_blocks() { return RED_BLOCKS; }
 
-cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const double* J, double c, double* Ainv,
+template <class S>
+cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const double* J, double c, S* Ainv, S* AinvT,
                                  int* status, cudaStream_t st) {
   ProfScope ps(PP_K_BLOCK_INVERSE, st);
-  k_block_inverse<<<m.ne, INV_THREADS, 0, st>>>(m, tb, J, c, Ainv, status);
+  k_block_inverse<S><<<m.ne, INV_THREADS, 0, st>>>(m, tb, J, c, Ainv, AinvT, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const double* J, double alpha, double beta,
-                                const double* x, double* y, int trans, cudaStream_t st) {
+template <class S>
+cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const S* J, double alpha, double beta,
+                                const S* x, S* y, int trans, cudaStream_t st) {
   ProfScope ps(PP_K_STAGE_MATVEC, st);
   const int g = m.ne, b = 128;
+#define PP_SMV(NBV)                                                                        \
+  case NBV:                                                                                \
+    if (trans) k_stage_matvec<NBV, true, S><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y);  \
+    else k_stage_matvec<NBV, false, S><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y);       \
+    break;
   switch (tb.nb) {
-    case 12: k_stage_matvec<12><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
-    case 24: k_stage_matvec<24><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
-    case 40: k_stage_matvec<40><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
-    case 60: k_stage_matvec<60><<<g, b, 0, st>>>(m, tb, J, alpha, beta, x, y, trans); break;
+    PP_SMV(12)
+    PP_SMV(24)
+    PP_SMV(40)
+    PP_SMV(60)
     default: return cudaErrorInvalidValue;
   }
+#undef PP_SMV
   return cudaGetLastError();
 }
 
-cudaError_t launch_block_apply(const DevMesh& m, int nb, const double* Ainv, const double* x, double* y, int trans,
+template <class S>
+cudaError_t launch_block_apply(const DevMesh& m, int nb, const S* Ainv, const S* x, S* y, int trans,
                                cudaStream_t st) {
   ProfScope ps(PP_K_BLOCK_APPLY, st);
   const int g = m.ne, b = 128;
+#define PP_BAP(NBV)                                                             \
+  case NBV:                                                                     \
+    if (trans) k_block_apply<NBV, true, S><<<g, b, 0, st>>>(m.ne, Ainv, x, y);   \
+    else k_block_apply<NBV, false, S><<<g, b, 0, st>>>(m.ne, Ainv, x, y);        \
+    break;
   switch (nb) {
-    case 12: k_block_apply<12><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
-    case 24: k_block_apply<24><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
-    case 40: k_block_apply<40><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
-    case 60: k_block_apply<60><<<g, b, 0, st>>>(m.ne, Ainv, x, y, trans); break;
+    PP_BAP(12)
+    PP_BAP(24)
+    PP_BAP(40)
+    PP_BAP(60)
     default: return cudaErrorInvalidValue;
   }
+#undef PP_BAP
   return cudaGetLastError();
 }
 
-cudaError_t launch_lincomb(int64_t n, double* y, int nterms, const double* c, const double* const* x,
-                           cudaStream_t st) {
+template <class Si, class So>
+cudaError_t launch_transpose_blocks(const DevMesh& m, int nb, const Si* J, So* JT, cudaStream_t st) {
   ProfScope ps(PP_K_OTHER, st);
-  k_lincomb<<<vec_blocks(n), 256, 0, st>>>(n, y, nterms, c[0], nterms > 1 ? c[1] : 0.0, nterms > 2 ? c[2] : 0.0,
-                                           nterms > 3 ? c[3] : 0.0, x[0], nterms > 1 ? x[1] : nullptr,
-                                           nterms > 2 ? x[2] : nullptr, nterms > 3 ? x[3] : nullptr);
+  k_transpose_blocks<Si, So><<<m.ne * 4, 256, 0, st>>>(m, nb, J, JT);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_dev(int64_t n, double* y, const double* a, const double* x, cudaStream_t st) {
+template <class S>
+cudaError_t launch_lincomb(int64_t n, S* y, int nterms, const double* c, const S* const* x, cudaStream_t st) {
   ProfScope ps(PP_K_OTHER, st);
-  k_scale_dev<<<vec_blocks(n), 256, 0, st>>>(n, y, a, x);
+  k_lincomb<S><<<vec_blocks(n), 256, 0, st>>>(n, y, nterms, c[0], nterms > 1 ? c[1] : 0.0, nterms > 2 ? c[2] : 0.0,
+                                              nterms > 3 ? c[3] : 0.0, x[0], nterms > 1 ? x[1] : nullptr,
+                                              nterms > 2 ? x[2] : nullptr, nterms > 3 ? x[3] : nullptr);
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_scale_dev(int64_t n, S* y, const double* a, const S* x, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_scale_dev<S><<<vec_blocks(n), 256, 0, st>>>(n, y, a, x);
+  return cudaGetLastError();
+}
+
+template <class Si, class So>
+cudaError_t launch_cast(int64_t n, So* y, const Si* x, cudaStream_t st) {
+  ProfScope ps(PP_K_OTHER, st);
+  k_cast<Si, So><<<vec_blocks(n), 256, 0, st>>>(n, y, x);
   return cudaGetLastError();
 }
 
@@ -642,62 +690,54 @@ cudaError_t launch_gmres_init(const double* bb, double rtol, double atol, int fi
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmres_givens(int j, int m, const double* h1, const double* h2, const double* nrm2, double* H,
-                                double* cs, double* sn, double* g, double* stat, cudaStream_t st) {
-  ProfScope ps(PP_K_OTHER, st);
-  k_gmres_givens<<<1, 32, 0, st>>>(j, m, h1, h2, nrm2, H, cs, sn, g, stat);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_gmres_backsolve(int ncols, int m, const double* H, const double* g, double* y, cudaStream_t st) {
   ProfScope ps(PP_K_OTHER, st);
   k_gmres_backsolve<<<1, 32, 0, st>>>(ncols, m, H, g, y);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaStream_t st) {
-  ProfScope ps(PP_K_OTHER, st);
-  k_scale<<<vec_blocks(n), 256, 0, st>>>(n, y, a, x);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* w, double* out,
-                        double* partial, unsigned* counter, cudaStream_t st) {
+template <class S>
+cudaError_t launch_mdot(int64_t n, const S* V, int64_t ldv, int k, const S* w, double* out, double* partial,
+                        unsigned* counter, cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
-  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(0, n, V, ldv, k, nullptr, const_cast<double*>(w), out, partial,
-                                                  counter, GivensArgs{});
+  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(0, n, V, ldv, k, nullptr, const_cast<S*>(w), out, partial,
+                                                     counter, GivensArgs{});
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
-                               double* out, double* partial, unsigned* counter, cudaStream_t st) {
+template <class S>
+cudaError_t launch_update_mdot(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
+                               double* partial, unsigned* counter, cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
-  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(1, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
+  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(1, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_norm2(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
-                                double* out, double* partial, unsigned* counter, cudaStream_t st) {
+template <class S>
+cudaError_t launch_update_norm2(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
+                                double* partial, unsigned* counter, cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
-  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
+  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_norm2_givens(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
-                                       double* out, double* partial, unsigned* counter, int j, int m,
-                                       const double* h1, const double* h2, double* H, double* cs, double* sn,
-                                       double* g, double* stat, cudaStream_t st) {
+template <class S>
+cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
+                                       double* partial, unsigned* counter, int j, int m, const double* h1,
+                                       const double* h2, double* H, double* cs, double* sn, double* g, double* stat,
+                                       cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
   GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat};
-  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, gv);
+  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, gv);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out, double* partial,
-                       unsigned* counter, cudaStream_t st) {
+template <class S>
+cudaError_t launch_dot(int64_t n, const S* x, const S* y, double* out, double* partial, unsigned* counter,
+                       cudaStream_t st) {
   ProfScope ps(PP_K_KRYLOV, st);
-  k_krylov<<<red_blocks(n), RED_THREADS, 0, st>>>(3, n, x, 0, 1, nullptr, const_cast<double*>(y), out, partial,
-                                                  counter, GivensArgs{});
+  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(3, n, x, 0, 1, nullptr, const_cast<S*>(y), out, partial,
+                                                     counter, GivensArgs{});
   return cudaGetLastError();
 }
 
@@ -707,5 +747,39 @@ cudaError_t launch_colsum(int ne, int k, const double* per_elem, double* out, do
   k_colsum<<<red_blocks(ne), RED_THREADS, 0, st>>>(ne, k, per_elem, out, partial, counter);
   return cudaGetLastError();
 }
+
+cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaStream_t st) {
+  const double c[1] = {a};
+  const double* xs[1] = {x};
+  return launch_lincomb<double>(n, y, 1, c, xs, st);
+}
+
+// ------------------------------------------------------------------ explicit instantiations
+#define PP_INST(S)                                                                                                    \
+  template cudaError_t launch_block_inverse<S>(const DevMesh&, const DevTables&, const double*, double, S*, S*,     \
+                                               int*, cudaStream_t);                                                 \
+  template cudaError_t launch_stage_matvec<S>(const DevMesh&, const DevTables&, const S*, double, double, const S*, \
+                                              S*, int, cudaStream_t);                                               \
+  template cudaError_t launch_block_apply<S>(const DevMesh&, int, const S*, const S*, S*, int, cudaStream_t);       \
+  template cudaError_t launch_lincomb<S>(int64_t, S*, int, const double*, const S* const*, cudaStream_t);           \
+  template cudaError_t launch_scale_dev<S>(int64_t, S*, const double*, const S*, cudaStream_t);                     \
+  template cudaError_t launch_mdot<S>(int64_t, const S*, int64_t, int, const S*, double*, double*, unsigned*,       \
+                                      cudaStream_t);                                                                \
+  template cudaError_t launch_update_mdot<S>(int64_t, const S*, int64_t, int, const double*, S*, double*, double*,  \
+                                             unsigned*, cudaStream_t);                                              \
+  template cudaError_t launch_update_norm2<S>(int64_t, const S*, int64_t, int, const double*, S*, double*, double*, \
+                                              unsigned*, cudaStream_t);                                             \
+  template cudaError_t launch_update_norm2_givens<S>(int64_t, const S*, int64_t, int, const double*, S*, double*,   \
+                                                     double*, unsigned*, int, int, const double*, const double*,    \
+                                                     double*, double*, double*, double*, double*, cudaStream_t);    \
+  template cudaError_t launch_dot<S>(int64_t, const S*, const S*, double*, double*, unsigned*, cudaStream_t);
+PP_INST(double)
+PP_INST(float)
+#undef PP_INST
+template cudaError_t launch_transpose_blocks<double, double>(const DevMesh&, int, const double*, double*,
+                                                             cudaStream_t);
+template cudaError_t launch_transpose_blocks<double, float>(const DevMesh&, int, const double*, float*, cudaStream_t);
+template cudaError_t launch_cast<double, float>(int64_t, float*, const double*, cudaStream_t);
+template cudaError_t launch_cast<float, double>(int64_t, double*, const float*, cudaStream_t);
 
 }  // namespace pp

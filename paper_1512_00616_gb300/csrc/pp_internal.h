@@ -127,44 +127,59 @@ cudaError_t launch_qoi_dframe(const DevMesh& m, const DevTables& tb, const Phys&
 cudaError_t launch_qoi_du(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
                           const double* u, double w0, double w1, double* g, cudaStream_t st);
 
-// Stage matrix A_e = detB_e Mref (x) I4 - c J_ee, inverted per element (Gauss-Jordan, partial pivoting).
-cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const double* J, double c, double* Ainv,
+// Linear-algebra wrappers, templated on the vector/matrix type S (double or float).
+// Stage matrix A_e = detB_e Mref (x) I4 - c J_ee (J in FP64), inverted per element by
+// Gauss-Jordan with partial pivoting in precision S; AinvT (nullable) receives the
+// transposed inverse.
+template <class S>
+cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const double* J, double c, S* Ainv, S* AinvT,
                                  int* status, cudaStream_t st);
-// y = alpha M x + beta J x  (trans = 0)  or  alpha M x + beta J^T x  (trans = 1); J may be null if beta == 0
-cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const double* J, double alpha, double beta,
-                                const double* x, double* y, int trans, cudaStream_t st);
+// y = alpha M x + beta J x (trans = 0) or alpha M x + beta J^T x (trans = 1); J may be null if beta == 0
+template <class S>
+cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const S* J, double alpha, double beta,
+                                const S* x, S* y, int trans, cudaStream_t st);
 // y = Ainv x (trans = 0) or Ainv^T x (trans = 1), per element
-cudaError_t launch_block_apply(const DevMesh& m, int nb, const double* Ainv, const double* x, double* y, int trans,
-                               cudaStream_t st);
+template <class S>
+cudaError_t launch_block_apply(const DevMesh& m, int nb, const S* Ainv, const S* x, S* y, int trans, cudaStream_t st);
+// JT: per element the transposed blocks of its block-column of J (output type may be narrower)
+template <class Si, class So>
+cudaError_t launch_transpose_blocks(const DevMesh& m, int nb, const Si* J, So* JT, cudaStream_t st);
+template <class Si, class So>
+cudaError_t launch_cast(int64_t n, So* y, const Si* x, cudaStream_t st);
 
 // vectors of length n
-cudaError_t launch_lincomb(int64_t n, double* y, int nterms, const double* c, const double* const* x,
+template <class S>
+cudaError_t launch_lincomb(int64_t n, S* y, int nterms, const double* c, const S* const* x,
                            cudaStream_t st);  // y = sum c_k x_k (y may alias one x_k)
 cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaStream_t st);  // y = a x
-cudaError_t launch_scale_dev(int64_t n, double* y, const double* a, const double* x, cudaStream_t st);  // y = a[0] x
+template <class S>
+cudaError_t launch_scale_dev(int64_t n, S* y, const double* a, const S* x, cudaStream_t st);  // y = a[0] x
 // device-side GMRES bookkeeping; stat = {res, tol, hn, 1/hn, beta, 1/beta, flag, j}
 cudaError_t launch_gmres_init(const double* bb, double rtol, double atol, int first, int m, double* g, double* stat,
                               cudaStream_t st);
-cudaError_t launch_gmres_givens(int j, int m, const double* h1, const double* h2, const double* nrm2, double* H,
-                                double* cs, double* sn, double* g, double* stat, cudaStream_t st);
 cudaError_t launch_gmres_backsolve(int ncols, int m, const double* H, const double* g, double* y, cudaStream_t st);
 // out[j] = V_j . w for j < k, V contiguous with stride ldv; deterministic two-level reduction
-cudaError_t launch_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* w, double* out,
-                        double* partial, unsigned* counter, cudaStream_t st);
+template <class S>
+cudaError_t launch_mdot(int64_t n, const S* V, int64_t ldv, int k, const S* w, double* out, double* partial,
+                        unsigned* counter, cudaStream_t st);
 // w -= V h[0:k]; then out[0:k] = V_j . w  (fused CGS second pass)
-cudaError_t launch_update_mdot(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
-                               double* out, double* partial, unsigned* counter, cudaStream_t st);
+template <class S>
+cudaError_t launch_update_mdot(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
+                               double* partial, unsigned* counter, cudaStream_t st);
 // w -= V h[0:k]; then out[0] = w . w
-cudaError_t launch_update_norm2(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
-                                double* out, double* partial, unsigned* counter, cudaStream_t st);
-// w -= V h[0:k]; out[0] = w . w; then the GMRES Givens update of column j (see launch_gmres_givens)
-cudaError_t launch_update_norm2_givens(int64_t n, const double* V, int64_t ldv, int k, const double* h, double* w,
-                                       double* out, double* partial, unsigned* counter, int j, int m,
-                                       const double* h1, const double* h2, double* H, double* cs, double* sn,
-                                       double* g, double* stat, cudaStream_t st);
+template <class S>
+cudaError_t launch_update_norm2(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
+                                double* partial, unsigned* counter, cudaStream_t st);
+// w -= V h[0:k]; out[0] = w . w; then the GMRES Givens update of Hessenberg column j
+template <class S>
+cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
+                                       double* partial, unsigned* counter, int j, int m, const double* h1,
+                                       const double* h2, double* H, double* cs, double* sn, double* g, double* stat,
+                                       cudaStream_t st);
 // out[0] = x . y
-cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out, double* partial,
-                       unsigned* counter, cudaStream_t st);
+template <class S>
+cudaError_t launch_dot(int64_t n, const S* x, const S* y, double* out, double* partial, unsigned* counter,
+                       cudaStream_t st);
 // out[j] = sum over elements of per_elem[e][j], j < k (k <= 8)
 cudaError_t launch_colsum(int ne, int k, const double* per_elem, double* out, double* partial, unsigned* counter,
                           cudaStream_t st);

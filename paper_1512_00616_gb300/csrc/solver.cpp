@@ -27,14 +27,17 @@ namespace pp {
 
 namespace {
 
-using Op = std::function<int(const double* x, double* y)>;
+template <class S>
+using OpT = std::function<int(const S* x, S* y)>;
+using Op = OpT<double>;
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-int host_dot(pp_ctx* ctx, int64_t n, const double* x, const double* y, double* out) {
-  PP_CK(launch_dot(n, x, y, ctx->d_scalar, ctx->d_partial, ctx->d_counter, ctx->stream));
+template <class S>
+int host_dot(pp_ctx* ctx, int64_t n, const S* x, const S* y, double* out) {
+  PP_CK(launch_dot<S>(n, x, y, ctx->d_scalar, ctx->d_partial, ctx->d_counter, ctx->stream));
   PP_CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   PP_CK(cudaStreamSynchronize(ctx->stream));
   *out = ctx->h_scalar[0];
@@ -43,15 +46,16 @@ int host_dot(pp_ctx* ctx, int64_t n, const double* x, const double* y, double* o
 
 int host_norm(pp_ctx* ctx, int64_t n, const double* x, double* out) {
   double d;
-  PP_TRY(host_dot(ctx, n, x, x, &d));
+  PP_TRY(host_dot<double>(ctx, n, x, x, &d));
   *out = std::sqrt(d);
   if (!std::isfinite(*out)) return set_error(ctx, PP_ENAN, "non-finite norm");
   return PP_OK;
 }
 
-int lincomb(pp_ctx* ctx, int64_t n, double* y, std::initializer_list<double> c, std::initializer_list<const double*> x) {
+template <class S>
+int lincomb(pp_ctx* ctx, int64_t n, S* y, std::initializer_list<double> c, std::initializer_list<const S*> x) {
   double cc[4];
-  const double* xx[4];
+  const S* xx[4];
   int k = 0;
   auto it = x.begin();
   for (double v : c) {
@@ -59,60 +63,69 @@ int lincomb(pp_ctx* ctx, int64_t n, double* y, std::initializer_list<double> c, 
     xx[k] = *it++;
     ++k;
   }
-  PP_CK(launch_lincomb(n, y, k, cc, xx, ctx->stream));
+  PP_CK(launch_lincomb<S>(n, y, k, cc, xx, ctx->stream));
   return PP_OK;
 }
 
-int copy(pp_ctx* ctx, int64_t n, double* y, const double* x) {
-  if (y != x) PP_CK(cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+int lincomb(pp_ctx* ctx, int64_t n, double* y, std::initializer_list<double> c,
+            std::initializer_list<const double*> x) {
+  return lincomb<double>(ctx, n, y, c, x);
+}
+
+template <class S>
+int copy(pp_ctx* ctx, int64_t n, S* y, const S* x) {
+  if (y != x) PP_CK(cudaMemcpyAsync(y, x, sizeof(S) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   return PP_OK;
 }
 
-// Right-preconditioned restarted GMRES for A x = b, x0 = 0.  Stops when
-// ||b - A x|| <= max(rtol ||b||, atol) (Arnoldi estimate) or after maxit Krylov
-// steps.  prec may be empty (no preconditioner).
+// Restarted GMRES for A x = b, x0 = 0, in vector type S.  Right-preconditioned
+// (x = P(V y)) or, with K.Z set and flexible = true, flexible (z_j = P(v_j) stored,
+// x = Z y) so that the preconditioner may change between iterations.  Stops when
+// ||b - A x|| <= max(rtol ||b||, atol) (Arnoldi estimate) or after maxit Krylov steps.
 //
 // The Hessenberg column, Givens rotations and residual estimate are kept on the
 // device; the host watches the convergence flag one Arnoldi step behind (event +
 // pinned copy per step), so the GPU queue never drains for a round trip.  The step
 // enqueued past convergence is simply not used (its column is beyond ncols).
-int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, double* x, double rtol, double atol,
-          int maxit, int* iters, double* res_out) {
+template <class S>
+int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const S* b, S* x, double rtol,
+          double atol, int maxit, int* iters, double* res_out, bool flexible = false) {
   const int64_t n = K.n;
   const int m = K.m;
   double* d_h1 = K.d_h;
   double* d_h2 = K.d_h + (m + 2);
   double* d_nrm = K.d_h + 2 * (m + 2);
-  PP_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
-  PP_TRY(copy(ctx, n, K.r, b));
+  const bool flex = flexible && K.Z && prec;
+  PP_CK(cudaMemsetAsync(x, 0, sizeof(S) * n, ctx->stream));
+  PP_TRY(copy<S>(ctx, n, K.r, b));
   int total = 0;
   bool first = true;
   double res = 0.0;
   int status = PP_ENOCONV;
   for (;;) {
-    // beta = ||r||, g = beta e1, tolerance fixed on the first cycle
-    PP_CK(launch_dot(n, K.r, K.r, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
+    PP_CK(launch_dot<S>(n, K.r, K.r, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
     PP_CK(launch_gmres_init(d_nrm, rtol, atol, first ? 1 : 0, m, K.d_g, K.d_stat, ctx->stream));
-    PP_CK(launch_scale_dev(n, K.V, K.d_stat + 5, K.r, ctx->stream));
+    PP_CK(launch_scale_dev<S>(n, K.V, K.d_stat + 5, K.r, ctx->stream));
     first = false;
     int ncols = 0;
     double flag = 0.0;
     for (int j = 0; j < m; ++j) {
-      double* vj = K.V + (size_t)j * n;
-      const double* z = vj;
+      S* vj = K.V + (size_t)j * n;
+      const S* z = vj;
       if (prec) {
-        PP_TRY(prec(vj, K.t));
-        z = K.t;
+        S* zj = flex ? K.Z + (size_t)j * n : K.t;
+        PP_TRY(prec(vj, zj));
+        z = zj;
       }
       PP_TRY(A(z, K.w));
-      PP_CK(launch_mdot(n, K.V, n, j + 1, K.w, d_h1, ctx->d_partial, ctx->d_counter, ctx->stream));
-      PP_CK(launch_update_mdot(n, K.V, n, j + 1, d_h1, K.w, d_h2, ctx->d_partial, ctx->d_counter, ctx->stream));
-      PP_CK(launch_update_norm2_givens(n, K.V, n, j + 1, d_h2, K.w, d_nrm, ctx->d_partial, ctx->d_counter, j, m, d_h1,
-                                       d_h2, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
+      PP_CK(launch_mdot<S>(n, K.V, n, j + 1, K.w, d_h1, ctx->d_partial, ctx->d_counter, ctx->stream));
+      PP_CK(launch_update_mdot<S>(n, K.V, n, j + 1, d_h1, K.w, d_h2, ctx->d_partial, ctx->d_counter, ctx->stream));
+      PP_CK(launch_update_norm2_givens<S>(n, K.V, n, j + 1, d_h2, K.w, d_nrm, ctx->d_partial, ctx->d_counter, j, m,
+                                          d_h1, d_h2, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
       double* slot = K.h_h + 8 * (j % kRing);
       PP_CK(cudaMemcpyAsync(slot, K.d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
-      PP_CK(launch_scale_dev(n, K.V + (size_t)(j + 1) * n, K.d_stat + 3, K.w, ctx->stream));
+      PP_CK(launch_scale_dev<S>(n, K.V + (size_t)(j + 1) * n, K.d_stat + 3, K.w, ctx->stream));
       ++total;
       // look one step behind
       const int jl = (j == m - 1) ? j : j - 1;
@@ -127,16 +140,17 @@ int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, 
         break;
       }
     }
-    if (ncols == 0) ncols = 1;  // m == 1 corner: one column
-    // x += P^{-1} V y
+    if (ncols == 0) ncols = 1;
+    // x += P(V y)  or  x += Z y
     PP_CK(launch_gmres_backsolve(ncols, m, K.d_H, K.d_g, K.d_y, ctx->stream));
-    PP_CK(cudaMemsetAsync(K.w, 0, sizeof(double) * n, ctx->stream));
-    PP_CK(launch_update_norm2(n, K.V, n, ncols, K.d_y, K.w, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
-    if (prec) {
+    PP_CK(cudaMemsetAsync(K.w, 0, sizeof(S) * n, ctx->stream));
+    PP_CK(launch_update_norm2<S>(n, flex ? K.Z : K.V, n, ncols, K.d_y, K.w, d_nrm, ctx->d_partial, ctx->d_counter,
+                                 ctx->stream));
+    if (prec && !flex) {
       PP_TRY(prec(K.w, K.t));
-      PP_TRY(lincomb(ctx, n, x, {1.0, 1.0}, {x, K.t}));
+      PP_TRY(lincomb<S>(ctx, n, x, {1.0, 1.0}, {x, K.t}));
     } else {
-      PP_TRY(lincomb(ctx, n, x, {1.0, 1.0}, {x, K.w}));
+      PP_TRY(lincomb<S>(ctx, n, x, {1.0, 1.0}, {x, K.w}));
     }
     if (flag == 1.0 || flag == 2.0) {
       status = PP_OK;
@@ -145,7 +159,7 @@ int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, 
     if (total >= maxit) break;
     // restart from the true residual r = b - A x
     PP_TRY(A(x, K.w));
-    PP_TRY(lincomb(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
+    PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
   }
   if (iters) *iters = total;
   if (res_out) *res_out = res;
@@ -154,37 +168,138 @@ int gmres(pp_ctx* ctx, Krylov& K, const Op& A, const Op& prec, const double* b, 
 
 struct StageView {
   const double* J;
-  const double* Ainv;
-  double c;  // a_ii dt
+  const double* Ainv;             // FP64 mode
+  double c;                       // a_ii dt
+  const double* JT = nullptr;     // transposed block-columns (optional)
+  const double* AinvT = nullptr;  // transposed inverses (optional, FP64 mode)
+  const float* J32 = nullptr;     // mixed mode FP32 copies
+  const float* JT32 = nullptr;
+  const float* A32 = nullptr;
+  const float* AT32 = nullptr;
 };
 
-int stage_solve(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans, const double* b, double* x,
-                double rtol, double atol, int* iters) {
+// FP32 GMRES on the FP32 stage operator (block-Jacobi FP32 preconditioner), b and x FP32.
+int stage_solve32(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans, const float* b, float* x,
+                  double rtol, int maxit, int* iters) {
   const DevMesh& m = mesh->dev;
+  const float* Jm = trans ? sv.JT32 : sv.J32;   // the transposed copies run through the normal kernels
+  const float* Am = trans ? sv.AT32 : sv.A32;
+  OpT<float> A = [&](const float* in, float* out) {
+    PP_CK(launch_stage_matvec<float>(m, ctx->tb, Jm, 1.0, -sv.c, in, out, 0, ctx->stream));
+    return PP_OK;
+  };
+  OpT<float> P = [&](const float* in, float* out) {
+    PP_CK(launch_block_apply<float>(m, ctx->tb.nb, Am, in, out, 0, ctx->stream));
+    return PP_OK;
+  };
+  int st = gmres<float>(ctx, ctx->k32, A, P, b, x, rtol, 0.0, maxit, iters, nullptr);
+  return st == PP_ENOCONV ? PP_OK : st;  // an inexact inner / Newton solve is acceptable
+}
+
+// Stage solve (M - c J) x = b or its transpose.  exact = false (primal Newton steps)
+// may be inexact; exact = true (tangent / adjoint) must reach rtol on the FP64 operator.
+int stage_solve(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans, const double* b, double* x,
+                double rtol, double atol, int* iters, bool exact) {
+  const DevMesh& m = mesh->dev;
+  const int64_t n = ctx->ws_nu;
+  if (ctx->cfg.precision == PP_PREC_MIXED) {
+    float* b32 = ctx->d_vec32;
+    float* x32 = ctx->d_vec32 + n;
+    if (!exact) {
+      PP_CK(launch_cast<double, float>(n, b32, b, ctx->stream));
+      PP_TRY(stage_solve32(ctx, mesh, sv, trans, b32, x32, rtol, ctx->cfg.gmres_maxit, iters));
+      PP_CK(launch_cast<float, double>(n, x, x32, ctx->stream));
+      return PP_OK;
+    }
+    // FP64 flexible GMRES on the exact operator, FP32 GMRES as the preconditioner
+    const bool useT = trans && sv.JT;
+    const double* Jm = useT ? sv.JT : sv.J;
+    const int tr = useT ? 0 : trans;
+    int inner_total = 0;
+    Op A = [&](const double* in, double* out) {
+      PP_CK(launch_stage_matvec<double>(m, ctx->tb, Jm, 1.0, -sv.c, in, out, tr, ctx->stream));
+      return PP_OK;
+    };
+    Op P = [&](const double* in, double* out) {
+      int it = 0;
+      PP_CK(launch_cast<double, float>(n, b32, in, ctx->stream));
+      PP_TRY(stage_solve32(ctx, mesh, sv, trans, b32, x32, ctx->cfg.inner_rtol, ctx->cfg.inner_maxit, &it));
+      PP_CK(launch_cast<float, double>(n, out, x32, ctx->stream));
+      inner_total += it;
+      return PP_OK;
+    };
+    int outer = 0;
+    int st = gmres<double>(ctx, ctx->kin, A, P, b, x, rtol, atol, ctx->cfg.gmres_maxit, &outer, nullptr, true);
+    if (iters) *iters = outer + inner_total;
+    if (st == PP_ENOCONV) return set_error(ctx, PP_ENOCONV, "stage FGMRES hit gmres_maxit");
+    return st;
+  }
+  // FP64 path: with stored transposes the transposed system uses the normal (row-streaming) kernels
+  const bool useT = trans && sv.JT && sv.AinvT;
+  const double* Jm = useT ? sv.JT : sv.J;
+  const double* Am = useT ? sv.AinvT : sv.Ainv;
+  const int tr = useT ? 0 : trans;
   Op A = [&](const double* in, double* out) {
-    PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 1.0, -sv.c, in, out, trans, ctx->stream));
+    PP_CK(launch_stage_matvec<double>(m, ctx->tb, Jm, 1.0, -sv.c, in, out, tr, ctx->stream));
     return PP_OK;
   };
   Op P = [&](const double* in, double* out) {
-    PP_CK(launch_block_apply(m, ctx->tb.nb, sv.Ainv, in, out, trans, ctx->stream));
+    PP_CK(launch_block_apply<double>(m, ctx->tb.nb, Am, in, out, tr, ctx->stream));
     return PP_OK;
   };
-  int st = gmres(ctx, ctx->kin, A, P, b, x, rtol, atol, ctx->cfg.gmres_maxit, iters, nullptr);
-  if (st == PP_ENOCONV) return set_error(ctx, PP_ENOCONV, "stage GMRES hit gmres_maxit");
+  int st = gmres<double>(ctx, ctx->kin, A, P, b, x, rtol, atol, ctx->cfg.gmres_maxit, iters, nullptr);
+  if (st == PP_ENOCONV) {
+    if (!exact) return PP_OK;
+    return set_error(ctx, PP_ENOCONV, "stage GMRES hit gmres_maxit");
+  }
   return st;
 }
 
 size_t nb2(const pp_ctx* ctx) { return (size_t)ctx->tb.nb * ctx->tb.nb; }
 
+StageView stage_view_slot(pp_ctx* ctx, size_t s, double c) {
+  const size_t ne = ctx->lin_mesh->ne;
+  StageView v{ctx->st_J + s * ne * 4 * nb2(ctx), ctx->st_Ainv ? ctx->st_Ainv + s * ne * nb2(ctx) : nullptr, c};
+  if (ctx->st_JT) v.JT = ctx->st_JT + s * ne * 4 * nb2(ctx);
+  if (ctx->st_AinvT) v.AinvT = ctx->st_AinvT + s * ne * nb2(ctx);
+  if (ctx->st_J32) {
+    v.J32 = ctx->st_J32 + s * ne * 4 * nb2(ctx);
+    v.JT32 = ctx->st_JT32 + s * ne * 4 * nb2(ctx);
+    v.A32 = ctx->st_A32 + s * ne * nb2(ctx);
+    v.AT32 = ctx->st_AT32 + s * ne * nb2(ctx);
+  }
+  return v;
+}
+
 StageView stored_stage(pp_ctx* ctx, int n, int i) {
-  size_t s = (size_t)n * 3 + i;
-  size_t ne = ctx->lin_mesh->ne;
-  return StageView{ctx->st_J + s * ne * 4 * nb2(ctx), ctx->st_Ainv + s * ne * nb2(ctx),
-                   ctx->A[i][i] * ctx->cfg.T / ctx->lin_Nt};
+  return stage_view_slot(ctx, (size_t)n * 3 + i, ctx->A[i][i] * ctx->cfg.T / ctx->lin_Nt);
 }
 
 const double* stored_u(pp_ctx* ctx, int n, int i) {
   return ctx->st_u + ((size_t)n * 3 + i) * ctx->ws_nu;
+}
+
+// Everything a stage slot stores from the FP64 Jacobian in slot J (already assembled):
+// preconditioner(s), transposed copies and FP32 copies, as the precision mode needs.
+int finalize_stage_slot(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, bool full) {
+  const DevMesh& m = mesh->dev;
+  const int nb = ctx->tb.nb;
+  const size_t nJ = (size_t)mesh->ne * 4 * nb2(ctx);
+  if (ctx->cfg.precision == PP_PREC_MIXED) {
+    PP_CK(launch_cast<double, float>((int64_t)nJ, const_cast<float*>(sv.J32), sv.J, ctx->stream));
+    PP_CK(launch_block_inverse<float>(m, ctx->tb, sv.J, sv.c, const_cast<float*>(sv.A32),
+                                      full ? const_cast<float*>(sv.AT32) : nullptr, ctx->d_status, ctx->stream));
+    if (full) {
+      PP_CK(launch_transpose_blocks<double, float>(m, nb, sv.J, const_cast<float*>(sv.JT32), ctx->stream));
+      if (sv.JT) PP_CK(launch_transpose_blocks<double, double>(m, nb, sv.J, const_cast<double*>(sv.JT), ctx->stream));
+    }
+    return PP_OK;
+  }
+  PP_CK(launch_block_inverse<double>(m, ctx->tb, sv.J, sv.c, const_cast<double*>(sv.Ainv),
+                                     full ? const_cast<double*>(sv.AinvT) : nullptr, ctx->d_status, ctx->stream));
+  if (full && sv.JT)
+    PP_CK(launch_transpose_blocks<double, double>(m, nb, sv.J, const_cast<double*>(sv.JT), ctx->stream));
+  return PP_OK;
 }
 
 }  // namespace
@@ -217,8 +332,8 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
   ctx->last_gmres_iters = 0;
   // chord Newton: all stages share a_ii = gamma, so the stored matrix of the previous
   // stage (exact at its converged state) is the Newton matrix until contraction slows
-  const double* Jn = nullptr;
-  const double* An = nullptr;
+  StageView nview{};
+  bool have_nview = false;
   for (int step = 0; step < Nt; ++step) {
     const double t0 = step * dt;
     for (int i = 0; i < 3; ++i) {
@@ -232,19 +347,19 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
       if (i == 2) PP_TRY(lincomb(ctx, n, base, {1.0, ctx->A[2][0], ctx->A[2][1]}, {u, k[0], k[1]}));
       PP_TRY(copy(ctx, n, k[i], i == 0 ? kprev : k[i - 1]));
       size_t slot = (size_t)step * 3 + i;
-      double* Js = ctx->st_J + slot * mesh->ne * 4 * nb2(ctx);
-      double* As = ctx->st_Ainv + slot * mesh->ne * nb2(ctx);
+      const StageView sview = stage_view_slot(ctx, slot, c);
+      double* Js = const_cast<double*>(sview.J);
       double* us = ctx->st_u + slot * n;
       double prev_res = INFINITY, alpha = 1.0;
       int backtracks = 0;
-      bool converged = false, refresh = (Jn == nullptr);
+      bool converged = false, refresh = !have_nview;
       for (int it = 0; it <= ctx->cfg.newton_maxit; ++it) {
         PP_TRY(lincomb(ctx, n, us, {1.0, ctx->A[i][i]}, {base, k[i]}));
         PP_CK(launch_residual(m, ctx->tb, ctx->ph, fr, us, r, ctx->stream));
-        PP_CK(launch_stage_matvec(m, ctx->tb, nullptr, 1.0, 0.0, k[i], R, 0, ctx->stream));
+        PP_CK(launch_stage_matvec<double>(m, ctx->tb, nullptr, 1.0, 0.0, k[i], R, 0, ctx->stream));
         PP_TRY(lincomb(ctx, n, R, {1.0, -dt}, {R, r}));
         double rn2, mun;
-        PP_TRY(host_dot(ctx, n, R, R, &rn2));
+        PP_TRY(host_dot<double>(ctx, n, R, R, &rn2));
         double rn = std::sqrt(rn2);
         // backtracking safeguard: a step that made the residual non-finite or larger is halved
         if (it > 0 && (!std::isfinite(rn) || rn > prev_res) && backtracks < 8) {
@@ -257,7 +372,7 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
         if (!std::isfinite(rn)) return set_error(ctx, PP_ENAN, "non-finite stage residual");
         if (it > 0 && rn > 0.25 * prev_res) refresh = true;  // slow chord contraction
         alpha = 1.0;
-        PP_CK(launch_stage_matvec(m, ctx->tb, nullptr, 1.0, 0.0, us, dk, 0, ctx->stream));
+        PP_CK(launch_stage_matvec<double>(m, ctx->tb, nullptr, 1.0, 0.0, us, dk, 0, ctx->stream));
         PP_TRY(host_norm(ctx, n, dk, &mun));
         const double tol = ctx->cfg.newton_tol * mun;
         if (rn <= tol || (it > 0 && rn <= 1e3 * tol && rn > 0.5 * prev_res)) {
@@ -268,26 +383,25 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
         if (refresh) {
           // Newton matrix at the current iterate (this stage's slot doubles as scratch)
           PP_CK(launch_jacobian(m, ctx->tb, ctx->ph, fr, us, Js, ctx->stream));
-          PP_CK(launch_block_inverse(m, ctx->tb, Js, c, As, ctx->d_status, ctx->stream));
-          Jn = Js;
-          An = As;
+          PP_TRY(finalize_stage_slot(ctx, mesh, sview, false));
+          nview = sview;
+          have_nview = true;
           refresh = false;
         }
         prev_res = rn;
         int gits = 0;
-        StageView sv{Jn, An, c};
-        int st = stage_solve(ctx, mesh, sv, 0, R, dk, ctx->cfg.gmres_rtol, 0.0, &gits);
+        int st = stage_solve(ctx, mesh, nview, 0, R, dk, ctx->cfg.gmres_rtol, 0.0, &gits, false);
         if (st != PP_OK && st != PP_ENOCONV) return st;
         ctx->last_gmres_iters += gits;
         PP_TRY(lincomb(ctx, n, k[i], {1.0, -1.0}, {k[i], dk}));
         ctx->last_newton_iters++;
       }
       if (converged) {
-        // exact Jacobian and preconditioner at the converged stage: the stored linearization
+        // exact Jacobian and preconditioner(s) at the converged stage: the stored linearization
         PP_CK(launch_jacobian(m, ctx->tb, ctx->ph, fr, us, Js, ctx->stream));
-        PP_CK(launch_block_inverse(m, ctx->tb, Js, c, As, ctx->d_status, ctx->stream));
-        Jn = Js;
-        An = As;
+        PP_TRY(finalize_stage_slot(ctx, mesh, sview, true));
+        nview = sview;
+        have_nview = true;
       }
       if (!converged) return set_error(ctx, PP_ENOCONV, "stage Newton did not converge");
       int status = 0;
@@ -356,9 +470,9 @@ int tangent_sweep(pp_ctx* ctx, const double* v, double* out) {
         PP_TRY(lincomb(ctx, n, w, {1.0, ctx->A[2][0], ctx->A[2][1]}, {du, dk[0], dk[1]}));
         win = w;
       }
-      PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 0.0, dt, win, rhs, 0, ctx->stream));
+      PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.J, 0.0, dt, win, rhs, 0, ctx->stream));
       int gits = 0;
-      PP_TRY(stage_solve(ctx, mesh, sv, 0, rhs, dk[i], ctx->cfg.lin_rtol, 0.0, &gits));
+      PP_TRY(stage_solve(ctx, mesh, sv, 0, rhs, dk[i], ctx->cfg.lin_rtol, 0.0, &gits, true));
       ctx->last_gmres_tangent += gits;
     }
     PP_TRY(lincomb(ctx, n, du, {1.0, ctx->b[0], ctx->b[1], ctx->b[2]}, {du, dk[0], dk[1], dk[2]}));
@@ -416,9 +530,10 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
                          {rhs, g[0], g[1], g[2]}));
       }
       int gits = 0;
-      PP_TRY(stage_solve(ctx, mesh, sv, 1, rhs, kap, ctx->cfg.lin_rtol, 0.0, &gits));
+      PP_TRY(stage_solve(ctx, mesh, sv, 1, rhs, kap, ctx->cfg.lin_rtol, 0.0, &gits, true));
       ctx->last_gmres_adjoint += gits;
-      PP_CK(launch_stage_matvec(m, ctx->tb, sv.J, 0.0, dt, kap, y[i], 1, ctx->stream));
+      if (sv.JT) PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.JT, 0.0, dt, kap, y[i], 0, ctx->stream));
+      else PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.J, 0.0, dt, kap, y[i], 1, ctx->stream));
       if (withF && dFdmu) {
         // kappa_i . dr/ds and w . dQ/ds for the motion seeds s = theta, theta', h'
         double sr[3], sq[3];
@@ -433,7 +548,7 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
           }
           fd.hd = Dual(fr.hd, s == 2 ? 1.0 : 0.0);
           PP_CK(launch_residual_dframe(m, ctx->tb, ctx->ph, fd, ui, dr, ctx->stream));
-          PP_CK(launch_dot(n, kap, dr, ctx->d_scalar + 16 + s, ctx->d_partial, ctx->d_counter, ctx->stream));
+          PP_CK(launch_dot<double>(n, kap, dr, ctx->d_scalar + 16 + s, ctx->d_partial, ctx->d_counter, ctx->stream));
           PP_CK(launch_qoi_dframe(m, ctx->tb, ctx->ph, fd, ui, ctx->d_elem, ctx->stream));
           PP_CK(launch_colsum(mesh->ne, 2, ctx->d_elem, ctx->d_scalar + 20 + 2 * s, ctx->d_partial, ctx->d_counter,
                               ctx->stream));
@@ -511,7 +626,8 @@ int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const
       return PP_OK;
     };
     int kits = 0;
-    int gs = gmres(ctx, K, A, Op(), Rsave, du, ctx->cfg.nk_gmres_rtol, 0.0, ctx->cfg.nk_max_krylov, &kits, nullptr);
+    int gs = gmres<double>(ctx, K, A, Op(), Rsave, du, ctx->cfg.nk_gmres_rtol, 0.0, ctx->cfg.nk_max_krylov, &kits,
+                           nullptr);
     if (gs != PP_OK && gs != PP_ENOCONV) return gs;
     st.krylov_iters += kits;
     PP_TRY(lincomb(ctx, n, u0_out, {1.0, -1.0}, {u0_out, du}));
@@ -549,7 +665,7 @@ int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_m
     return PP_OK;
   };
   int kits = 0;
-  int gs = gmres(ctx, K, A, Op(), d, x, 0.0, ctx->cfg.adj_tol, ctx->cfg.adj_maxit, &kits, nullptr);
+  int gs = gmres<double>(ctx, K, A, Op(), d, x, 0.0, ctx->cfg.adj_tol, ctx->cfg.adj_maxit, &kits, nullptr);
   if (gs != PP_OK && gs != PP_ENOCONV) return gs;
   // final sweep with the periodic final condition: multipliers and gradient
   PP_TRY(adjoint_sweep(ctx, x, weights, z, dFdmu));
