@@ -36,7 +36,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c1")
-    ap.add_argument("--roofline-kernel", default="jacobian")
+    ap.add_argument("--roofline-kernel", default="stage_matvec")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -242,12 +242,22 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c):
         return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
                 "frac": ach / fp64_tflops if fp64_tflops else None, "traffic": None,
                 "kernel": "k_jacobian", "launches": res["kern_launches"], "avg_us": t * 1e6}
-    if kernel in ("stage_matvec", "block_apply"):
-        blocks = 4 if kernel == "stage_matvec" else 1
-        byts = ne * (blocks * nb * nb * 8 + 2 * nb * 8)
+    if kernel in ("stage_matvec", "block_apply", "stage_matvec32", "block_apply32"):
+        blocks = 4 if kernel.startswith("stage_matvec") else 1
+        word = 4 if kernel.endswith("32") else 8
+        byts = ne * (blocks * nb * nb * word + 2 * nb * word)
+        if word == 8:
+            # GB300 issues ~2 FP64 FMA per clock per SM: the FP64 block product is FP64-ALU bound
+            # (its FMA floor exceeds its HBM floor), so it is held against the measured FP64 peak
+            flops = 2.0 * ne * blocks * nb * nb
+            ach = flops / t / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
+                    "frac": ach / fp64_tflops if fp64_tflops else None, "traffic": None,
+                    "kernel": "k_" + kernel.replace("32", "") + "<double>", "launches": res["kern_launches"],
+                    "avg_us": t * 1e6, "hbm_gbs_equiv": byts / t / 1e9}
         ach = byts / t / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "k_" + kernel,
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "k_" + kernel.replace("32", "") + "<float>",
                 "launches": res["kern_launches"], "avg_us": t * 1e6}
     return None
 

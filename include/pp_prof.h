@@ -21,7 +21,10 @@ extern "C" {
 #define PP_K_BLOCK_INVERSE 5 /* batched Gauss-Jordan inversion of the stage diagonal blocks */
 #define PP_K_KRYLOV 6        /* fused multi-dot / update / norm reductions */
 #define PP_K_OTHER 7         /* vector combinations, QoI and column-sum kernels */
-#define PP_K_COUNT 8
+#define PP_K_STAGE_MATVEC32 8  /* FP32 block-sparse product (mixed-precision inner solves) */
+#define PP_K_BLOCK_APPLY32 9   /* FP32 block-Jacobi application */
+#define PP_K_KRYLOV32 10       /* FP32 Krylov reductions */
+#define PP_K_COUNT 11
 
 /* Starts timing every launch of kernel class `kind` (one class at a time; PP_K_NONE
    stops).  Resets the accumulated totals.  Not thread-safe: one host thread drives libpp. */

@@ -27,7 +27,8 @@ EXPORTED = [
     # include/pp_prof.h
     "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
 ]
-PP_K = dict(none=0, jacobian=1, residual=2, stage_matvec=3, block_apply=4, block_inverse=5, krylov=6, other=7)
+PP_K = dict(none=0, jacobian=1, residual=2, stage_matvec=3, block_apply=4, block_inverse=5, krylov=6, other=7,
+            stage_matvec32=8, block_apply32=9, krylov32=10)
 
 
 class pp_config(C.Structure):
@@ -253,7 +254,7 @@ def pp_prof_read():
 
 
 def pp_prof_counts():
-    a = (C.c_int64 * 8)()
+    a = (C.c_int64 * 11)()
     _check(None, _lib.pp_prof_counts(a))
     return {k: a[v] for k, v in PP_K.items() if k != "none"}
 

@@ -614,7 +614,7 @@ cudaError_t launch_block_inverse(const DevMesh& m, const DevTables& tb, const do
 template <class S>
 cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const S* J, double alpha, double beta,
                                 const S* x, S* y, int trans, cudaStream_t st) {
-  ProfScope ps(PP_K_STAGE_MATVEC, st);
+  ProfScope ps(sizeof(S) == 8 ? PP_K_STAGE_MATVEC : PP_K_STAGE_MATVEC32, st);
   const int g = m.ne, b = 128;
 #define PP_SMV(NBV)                                                                        \
   case NBV:                                                                                \
@@ -635,7 +635,7 @@ cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const S* 
 template <class S>
 cudaError_t launch_block_apply(const DevMesh& m, int nb, const S* Ainv, const S* x, S* y, int trans,
                                cudaStream_t st) {
-  ProfScope ps(PP_K_BLOCK_APPLY, st);
+  ProfScope ps(sizeof(S) == 8 ? PP_K_BLOCK_APPLY : PP_K_BLOCK_APPLY32, st);
   const int g = m.ne, b = 128;
 #define PP_BAP(NBV)                                                             \
   case NBV:                                                                     \
@@ -699,7 +699,7 @@ cudaError_t launch_gmres_backsolve(int ncols, int m, const double* H, const doub
 template <class S>
 cudaError_t launch_mdot(int64_t n, const S* V, int64_t ldv, int k, const S* w, double* out, double* partial,
                         unsigned* counter, cudaStream_t st) {
-  ProfScope ps(PP_K_KRYLOV, st);
+  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
   k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(0, n, V, ldv, k, nullptr, const_cast<S*>(w), out, partial,
                                                      counter, GivensArgs{});
   return cudaGetLastError();
@@ -708,7 +708,7 @@ cudaError_t launch_mdot(int64_t n, const S* V, int64_t ldv, int k, const S* w, d
 template <class S>
 cudaError_t launch_update_mdot(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
                                double* partial, unsigned* counter, cudaStream_t st) {
-  ProfScope ps(PP_K_KRYLOV, st);
+  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
   k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(1, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
   return cudaGetLastError();
 }
@@ -716,7 +716,7 @@ cudaError_t launch_update_mdot(int64_t n, const S* V, int64_t ldv, int k, const 
 template <class S>
 cudaError_t launch_update_norm2(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
                                 double* partial, unsigned* counter, cudaStream_t st) {
-  ProfScope ps(PP_K_KRYLOV, st);
+  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
   k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
   return cudaGetLastError();
 }
@@ -726,7 +726,7 @@ cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k
                                        double* partial, unsigned* counter, int j, int m, const double* h1,
                                        const double* h2, double* H, double* cs, double* sn, double* g, double* stat,
                                        cudaStream_t st) {
-  ProfScope ps(PP_K_KRYLOV, st);
+  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
   GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat};
   k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, gv);
   return cudaGetLastError();
@@ -735,7 +735,7 @@ cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k
 template <class S>
 cudaError_t launch_dot(int64_t n, const S* x, const S* y, double* out, double* partial, unsigned* counter,
                        cudaStream_t st) {
-  ProfScope ps(PP_K_KRYLOV, st);
+  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
   k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(3, n, x, 0, 1, nullptr, const_cast<S*>(y), out, partial,
                                                      counter, GivensArgs{});
   return cudaGetLastError();
