@@ -133,6 +133,25 @@ int pp_jacobian_blocks(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n
 int pp_qoi_rate(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double t, const double* u,
                 double* out);
 
+/* Same result as pp_qoi_rate, but this call allocates no memory: it never calls
+   cudaMalloc, cudaFree or an allocating library routine.  It is for callers that may
+   not allocate, for example code under an allocator that forbids outside allocations,
+   or code that must not allocate after start-up.  (The paper has no counterpart; this
+   is a service entry point of the library.)
+   - Scratch: one static device array of 1 MiB + 33 KiB per device that loads the library,
+     kept until the process exits.  Meshes of more than 65536 elements are rejected with
+     PP_EINVAL.
+   - First call: the first call on a device looks up the array's device address
+     (cudaGetSymbolAddress) with that device current.  Make this first call before any
+     stream capture.
+   - Concurrency: every call shares the one array.  Calls that overlap on the GPU, e.g.
+     on different streams or from different contexts on the same device, race.  The
+     finishing counter is cleared at the start of each call; other contents are
+     overwritten.
+   - Arguments: as pp_qoi_rate.  u: DEVICE; out: HOST [2] = (P^h, F_x^h). */
+int pp_qoi_rate_noalloc(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double t, const double* u,
+                        double* out);
+
 /* Primal sweep u^(Nt)(u0; mu) over one period (Eq. dirk2) with Nt equal DIRK3
    steps of dt = T/Nt (T from the config).  u0: DEVICE [N_u].  u_traj: DEVICE
    [(Nt+1)][N_u] or NULL.  u_final: DEVICE [N_u] or NULL.  qoi: HOST [4] or NULL:

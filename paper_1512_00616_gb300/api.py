@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "PP_OK", -1: "PP_EINVAL", -2: "PP_ENOMEM", -3: "PP_ENOCONV", 
 EXPORTED = [
     "pp_version", "pp_config_default", "pp_create", "pp_destroy", "pp_last_error", "pp_mesh_create",
     "pp_mesh_destroy", "pp_mesh_info", "pp_residual", "pp_jacobian_blocks", "pp_qoi_rate", "pp_primal_period",
-    "pp_tangent_matvec", "pp_adjoint_sweep", "pp_shoot_nk", "pp_periodic_adjoint",
+    "pp_tangent_matvec", "pp_adjoint_sweep", "pp_shoot_nk", "pp_periodic_adjoint", "pp_qoi_rate_noalloc",
     # include/pp_prof.h
     "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
 ]
@@ -76,6 +76,7 @@ def _load():
         "pp_residual": (I, [P, P, dp, I, D, P, P]),
         "pp_jacobian_blocks": (I, [P, P, dp, I, D, P, P]),
         "pp_qoi_rate": (I, [P, P, dp, I, D, P, dp]),
+        "pp_qoi_rate_noalloc": (I, [P, P, dp, I, D, P, dp]),
         "pp_primal_period": (I, [P, P, dp, I, P, I, P, P, dp]),
         "pp_tangent_matvec": (I, [P, P, P]),
         "pp_adjoint_sweep": (I, [P, P, dp, P, dp]),
@@ -187,6 +188,13 @@ def pp_qoi_rate(ctx, mesh, mu, t, u):
     m, mp = _host(mu)
     out = np.zeros(2)
     _check(ctx, _lib.pp_qoi_rate(ctx, mesh, mp, len(m), float(t), _dev(u, "u"), _host(out)[1]))
+    return out
+
+
+def pp_qoi_rate_noalloc(ctx, mesh, mu, t, u):
+    m, mp = _host(mu)
+    out = np.zeros(2)
+    _check(ctx, _lib.pp_qoi_rate_noalloc(ctx, mesh, mp, len(m), float(t), _dev(u, "u"), _host(out)[1]))
     return out
 
 
