@@ -177,7 +177,15 @@ int pp_tangent_matvec(pp_ctx* ctx, const double* v, double* out);
    (Eq. funcl-grad-nosens-dirk) evaluated with this sweep's multipliers. */
 int pp_adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, double* lam0, double* dFdmu);
 
+/* Steady flow with the airfoil frozen at its t = 0 pose and the mesh at rest: the
+   paper's "steady-state flow" initial guess for shooting (Sec. 6.1).  Pseudo-transient
+   continuation from the free stream until ||r(u)||_2 <= tol ||r(u_inf)||_2.
+   u: DEVICE [N_u] output.  steps, rel_res: HOST or NULL.  Errors: PP_ENOCONV. */
+int pp_steady_state(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double tol, int maxit, double* u,
+                    int* steps, double* rel_res);
+
 typedef struct pp_shoot_stats {
+  int cold_start;            /* 0 caller's guess, 1 free stream (steady state stalled), 2 steady state */
   int newton_iters;          /* shooting Newton iterations taken */
   int krylov_iters;          /* tangent sweeps (GMRES matvecs) in total */
   int primal_sweeps;
@@ -187,8 +195,9 @@ typedef struct pp_shoot_stats {
 } pp_shoot_stats;
 
 /* Newton-Krylov shooting (Algorithm primal): solves u^(Nt)(u0; mu) = u0 to
-   ||u^(Nt)(u0) - u0||_2 <= tol.  u0_guess: DEVICE [N_u] or NULL (NULL = free
-   stream).  u0_out: DEVICE [N_u] (may alias u0_guess).  qoi: HOST [4] or NULL
+   ||u^(Nt)(u0) - u0||_2 <= tol.  u0_guess: DEVICE [N_u] or NULL (NULL = the
+   steady flow of pp_steady_state, or the free stream if that stalls; see
+   stats->cold_start).  u0_out: DEVICE [N_u] (may alias u0_guess).  qoi: HOST [4] or NULL
    (as in pp_primal_period, at the returned u0).  On return the stored
    linearization is that of the returned u0.  stats: HOST or NULL.
    Errors: PP_ENOCONV (u0_out then holds the last iterate). */

@@ -256,7 +256,11 @@ class DG:
         return th, thdot, hdot
 
     def frame(self, mu, t):
-        th, thd, hd = self.motion(mu, t)
+        if t is None:  # frozen pose of t = 0 with the mesh at rest (steady-state problem)
+            th, _, _ = self.motion(mu, 0.0)
+            thd, hd = 0.0 * th, 0.0 * th
+        else:
+            th, thd, hd = self.motion(mu, t)
         c, s = np.cos(th), np.sin(th)
         Q = np.array([[c, s], [-s, c]])
         Qd = thd * np.array([[-s, c], [-c, -s]])
@@ -308,7 +312,8 @@ class DG:
 
     def residual_local(self, uS, uN, mu, t):
         """r_e from the element's own state uS [..., Ne, 4, Np] and face-neighbour states
-        uN [..., Ne, 3, 4, Np] (boundary slots ignored)."""
+        uN [..., Ne, 3, 4, Np] (boundary slots ignored).  t = None: the airfoil frozen at
+        its t = 0 pose with the mesh at rest (the steady-state problem)."""
         Q, Qd, hd = self.frame(mu, t)
         P = np.einsum("dk,ekl->edl", Q, self.BinvT)                      # grad_x = P grad_xi
         g = self.gam

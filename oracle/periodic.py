@@ -248,3 +248,29 @@ def dense_phi_T(dg, tr):
     """Brute force d lambda^(0)/d lambda_Nt, one adjoint sensitivity sweep per column."""
     n = dg.Nu
     return np.stack([adjoint_sweep(dg, tr, np.eye(n)[:, j])[0] for j in range(n)], 1)
+
+
+def steady_state(dg, mu, u0, tol=1e-12, maxit=200, dtau0=0.1, dtau_max=1e4):
+    """Steady flow at the t = 0 pose with the mesh at rest (the paper's cold start, Sec. 6.1),
+    by pseudo-transient continuation: backward-Euler pseudo steps (M - dtau J) du = dtau r(u)
+    with the pseudo step grown by the residual ratio (switched evolution relaxation) and cut
+    on a rejected step.  Stops when ||r|| <= tol ||r(u0)||."""
+    M = dg.mass()
+    u = np.array(u0, dtype=np.float64).reshape(-1)
+    r = dg.residual(u, mu, None)
+    rn0 = rn = np.linalg.norm(r)
+    dtau = dtau0
+    for it in range(maxit):
+        if rn <= tol * rn0:
+            return u, it, rn / rn0
+        A = (M - dtau * dg.jacobian(u, mu, None)).tocsc()
+        du = spla.splu(A).solve(dtau * r)
+        ut = u + du
+        rt = dg.residual(ut, mu, None)
+        rnt = np.linalg.norm(rt)
+        if np.isfinite(rnt) and rnt < 2.0 * rn:
+            dtau = min(dtau * min(max(rn / rnt, 0.5), 4.0), dtau_max)
+            u, r, rn = ut, rt, rnt
+        else:
+            dtau *= 0.25
+    raise RuntimeError("oracle pseudo-transient continuation did not converge")

@@ -24,6 +24,7 @@ EXPORTED = [
     "pp_version", "pp_config_default", "pp_create", "pp_destroy", "pp_last_error", "pp_mesh_create",
     "pp_mesh_destroy", "pp_mesh_info", "pp_residual", "pp_jacobian_blocks", "pp_qoi_rate", "pp_primal_period",
     "pp_tangent_matvec", "pp_adjoint_sweep", "pp_shoot_nk", "pp_periodic_adjoint", "pp_qoi_rate_noalloc",
+    "pp_steady_state",
     # include/pp_prof.h
     "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
 ]
@@ -43,7 +44,7 @@ class pp_config(C.Structure):
 
 
 class pp_shoot_stats(C.Structure):
-    _fields_ = [("newton_iters", C.c_int), ("krylov_iters", C.c_int), ("primal_sweeps", C.c_int),
+    _fields_ = [("cold_start", C.c_int), ("newton_iters", C.c_int), ("krylov_iters", C.c_int), ("primal_sweeps", C.c_int),
                 ("stage_newton_iters", C.c_int), ("residual", C.c_double * 64), ("seconds", C.c_double)]
 
 
@@ -77,6 +78,7 @@ def _load():
         "pp_jacobian_blocks": (I, [P, P, dp, I, D, P, P]),
         "pp_qoi_rate": (I, [P, P, dp, I, D, P, dp]),
         "pp_qoi_rate_noalloc": (I, [P, P, dp, I, D, P, dp]),
+        "pp_steady_state": (I, [P, P, dp, I, D, I, P, C.POINTER(I), dp]),
         "pp_primal_period": (I, [P, P, dp, I, P, I, P, P, dp]),
         "pp_tangent_matvec": (I, [P, P, P]),
         "pp_adjoint_sweep": (I, [P, P, dp, P, dp]),
@@ -230,10 +232,18 @@ def pp_shoot_nk(ctx, mesh, mu, Nt, tol, u0_out, u0_guess=None, raise_on_noconv=T
     if code != PP_ENOCONV or raise_on_noconv:
         _check(ctx, code)
     n = min(st.newton_iters + 1, 64)
-    stats = dict(newton_iters=st.newton_iters, krylov_iters=st.krylov_iters, primal_sweeps=st.primal_sweeps,
+    stats = dict(cold_start=st.cold_start, newton_iters=st.newton_iters, krylov_iters=st.krylov_iters, primal_sweeps=st.primal_sweeps,
                  stage_newton_iters=st.stage_newton_iters, residual=list(st.residual[:n]), seconds=st.seconds,
                  status=code)
     return qoi, stats
+
+
+def pp_steady_state(ctx, mesh, mu, u, tol=1e-10, maxit=100):
+    m, mp = _host(mu)
+    steps, rel = C.c_int(), C.c_double()
+    _check(ctx, _lib.pp_steady_state(ctx, mesh, mp, len(m), float(tol), int(maxit), _dev(u, "u"), C.byref(steps),
+                                     C.byref(rel)))
+    return steps.value, rel.value
 
 
 def pp_periodic_adjoint(ctx, mesh, mu, Nt, weights, u0=None, lam_Nt=None):

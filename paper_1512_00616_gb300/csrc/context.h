@@ -126,6 +126,8 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
                  double* u_traj, double* u_final, double* qoi);
 int tangent_sweep(pp_ctx* ctx, const double* v, double* out);
 int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, double* lam0, double* dFdmu);
+int steady_state(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double* u, double tol, int maxit,
+                 int* steps, double* rel_res);
 int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess, int Nt,
              double tol, double* u0_out, double* qoi, pp_shoot_stats* stats);
 int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,

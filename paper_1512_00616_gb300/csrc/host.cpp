@@ -697,6 +697,15 @@ int pp_shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, co
   return shoot_nk(ctx, mesh, mu, n_mu, u0_guess, Nt, tol, u0_out, qoi, stats);
 }
 
+int pp_steady_state(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double tol, int maxit, double* u,
+                    int* steps, double* rel_res) {
+  if (!ctx || !mesh || !mu || !u || !(tol > 0) || maxit < 1)
+    return set_error(ctx, PP_EINVAL, "pp_steady_state: bad argument");
+  PP_TRY(check_mu(ctx, n_mu));
+  PP_CK(cudaSetDevice(ctx->device));
+  return steady_state(ctx, mesh, mu, n_mu, u, tol, maxit, steps, rel_res);
+}
+
 int pp_periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
                         const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats) {
   if (!ctx || !mesh || !mu || !weights || !dFdmu || Nt < 1)

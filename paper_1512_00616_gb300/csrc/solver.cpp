@@ -578,6 +578,78 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
   return PP_OK;
 }
 
+// --------------------------------------------------------------------------- steady state
+// Pseudo-transient continuation for r(u; theta(0), mesh at rest) = 0: backward-Euler pseudo
+// steps (M - dtau J) du = dtau r(u), dtau grown by the residual ratio (switched evolution
+// relaxation) and cut on a rejected step.  FP64 block-Jacobi GMRES, work buffers of the
+// context.  Starts from the free stream.
+int steady_state(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double* u, double tol, int maxit,
+                 int* steps, double* rel_res) {
+  PP_TRY(ensure_workspace(ctx, mesh));
+  const DevMesh& m = mesh->dev;
+  const int64_t n = ctx->ws_nu;
+  Motion mo = motion(ctx, mu, n_mu, 0.0);
+  mo.thd = 0.0;
+  mo.hd = 0.0;
+  FrameT<double> fr = frame_of(mo);
+  {
+    std::vector<double> fs(n);
+    const int nb = ctx->tb.nb, Np = ctx->tb.Np;
+    for (int64_t e = 0; e < mesh->ne; ++e)
+      for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < Np; ++i) fs[e * nb + a * Np + i] = ctx->ph.Uinf[a];
+    PP_CK(cudaMemcpyAsync(u, fs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    PP_CK(cudaStreamSynchronize(ctx->stream));
+  }
+  double* r = work_vec(ctx, 0);
+  double* rt = work_vec(ctx, 1);
+  double* du = work_vec(ctx, 2);
+  double* ut = work_vec(ctx, 3);
+  double* rhs = work_vec(ctx, 4);
+  PP_CK(launch_residual(m, ctx->tb, ctx->ph, fr, u, r, ctx->stream));
+  double rn0, rn;
+  PP_TRY(host_norm(ctx, n, r, &rn0));
+  rn = rn0;
+  double dtau = 0.1;
+  const double dtau_max = 1e4;
+  int it = 0;
+  for (; it < maxit; ++it) {
+    if (rn <= tol * rn0) break;
+    PP_CK(launch_jacobian(m, ctx->tb, ctx->ph, fr, u, ctx->d_J, ctx->stream));
+    PP_CK(launch_block_inverse<double>(m, ctx->tb, ctx->d_J, dtau, ctx->d_Ainv, nullptr, ctx->d_status, ctx->stream));
+    PP_TRY(lincomb(ctx, n, rhs, {dtau}, {r}));
+    Op A = [&](const double* in, double* out) {
+      PP_CK(launch_stage_matvec<double>(m, ctx->tb, ctx->d_J, 1.0, -dtau, in, out, 0, ctx->stream));
+      return PP_OK;
+    };
+    Op P = [&](const double* in, double* out) {
+      PP_CK(launch_block_apply<double>(m, ctx->tb.nb, ctx->d_Ainv, in, out, 0, ctx->stream));
+      return PP_OK;
+    };
+    int gits = 0;
+    int st = gmres<double>(ctx, ctx->kin, A, P, rhs, du, 1e-4, 0.0, ctx->cfg.gmres_maxit, &gits, nullptr);
+    if (st != PP_OK && st != PP_ENOCONV) return st;
+    PP_TRY(lincomb(ctx, n, ut, {1.0, 1.0}, {u, du}));
+    PP_CK(launch_residual(m, ctx->tb, ctx->ph, fr, ut, rt, ctx->stream));
+    double d2;
+    PP_TRY(host_dot<double>(ctx, n, rt, rt, &d2));
+    const double rnt = std::sqrt(d2);
+    if (std::isfinite(rnt) && rnt < 2.0 * rn) {
+      dtau = std::fmin(dtau * std::fmin(std::fmax(rn / rnt, 0.5), 4.0), dtau_max);
+      PP_TRY(copy(ctx, n, u, ut));
+      PP_TRY(copy(ctx, n, r, rt));
+      rn = rnt;
+    } else {
+      dtau *= 0.25;
+    }
+  }
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  if (steps) *steps = it;
+  if (rel_res) *rel_res = rn / rn0;
+  if (rn > tol * rn0) return set_error(ctx, PP_ENOCONV, "pseudo-transient continuation did not converge");
+  return PP_OK;
+}
+
 // --------------------------------------------------------------------------- shooting
 int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess, int Nt,
              double tol, double* u0_out, double* qoi, pp_shoot_stats* stats) {
@@ -588,14 +660,23 @@ int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const
   // u0 lives in u0_out; the outer Krylov level owns V, w, t, r
   if (u0_guess) {
     PP_TRY(copy(ctx, n, u0_out, u0_guess));
+    st.cold_start = 0;
   } else {
-    std::vector<double> fs(n);
-    const int nb = ctx->tb.nb, Np = ctx->tb.Np;
-    for (int64_t e = 0; e < mesh->ne; ++e)
-      for (int a = 0; a < 4; ++a)
-        for (int i = 0; i < Np; ++i) fs[e * nb + a * Np + i] = ctx->ph.Uinf[a];
-    PP_CK(cudaMemcpyAsync(u0_out, fs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
-    PP_CK(cudaStreamSynchronize(ctx->stream));
+    // cold start: the steady flow at the t = 0 pose (Sec. 6.1); free stream if that stalls
+    int steps = 0;
+    double rr = 0.0;
+    int ss = steady_state(ctx, mesh, mu, n_mu, u0_out, 1e-8, 100, &steps, &rr);
+    st.cold_start = ss == PP_OK ? 2 : 1;
+    if (ss != PP_OK) {
+      if (ss != PP_ENOCONV && ss != PP_ENAN) return ss;
+      std::vector<double> fs(n);
+      const int nb = ctx->tb.nb, Np = ctx->tb.Np;
+      for (int64_t e = 0; e < mesh->ne; ++e)
+        for (int a = 0; a < 4; ++a)
+          for (int i = 0; i < Np; ++i) fs[e * nb + a * Np + i] = ctx->ph.Uinf[a];
+      PP_CK(cudaMemcpyAsync(u0_out, fs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+      PP_CK(cudaStreamSynchronize(ctx->stream));
+    }
   }
   // outer-level scratch: the last three outer Krylov vectors are free between GMRES calls
   Krylov& K = ctx->kout;

@@ -262,3 +262,22 @@ def test_error_codes():
         A.pp_mesh_destroy(m)
     finally:
         A.pp_destroy(ctx)
+
+
+def test_steady_state_parity_and_cold_start():
+    c = CONFIGS["c0"]
+    mesh = config_mesh("c0")
+    dg = DG(mesh, c["p"], kin=c["kin"])
+    u_ref, _, _ = OP.steady_state(dg, MU_C0, free_stream_state(dg.Ne, c["p"]).reshape(-1), tol=1e-12)
+    A, ctx, m = make(c["p"], c["kin"], mesh, **TIGHT)
+    try:
+        u = torch.zeros(dg.Nu, dtype=torch.float64, device="cuda")
+        steps, rel = A.pp_steady_state(ctx, m, MU_C0, u, tol=1e-12, maxit=100)
+        assert rel <= 1e-12
+        assert rel_err(to_host(u), u_ref) <= PARITY_TOL
+        u0 = torch.zeros_like(u)
+        qoi, st = A.pp_shoot_nk(ctx, m, MU_C0, c["Nt"], 1e-10, u0)
+        assert st["cold_start"] == 2 and st["residual"][-1] <= 1e-10
+    finally:
+        A.pp_mesh_destroy(m)
+        A.pp_destroy(ctx)

@@ -156,3 +156,18 @@ def test_fluid_at_rest_exerts_no_net_force():
     u = np.broadcast_to(U[None, :, None], (dg.Ne, 4, dg.Np)).reshape(-1).copy()
     pw, fx = dg.qoi_rate(u, np.zeros(3), 0.0)
     assert abs(fx) < 1e-12 and abs(pw) < 1e-12
+
+
+def test_steady_state_is_a_root_of_the_frozen_residual():
+    """The cold start of Sec. 6.1 is the steady flow at the t = 0 pose with the mesh at
+    rest: a root of r(u; theta(0), v_G = 0).  PTC must reach it from the free stream."""
+    from oracle import periodic as P
+    dg = D.DG(ogrid(12, 2, seed=0), 1)
+    u_inf = free_stream_state(dg.Ne, 1).reshape(-1)
+    u, it, rr = P.steady_state(dg, MU_C0, u_inf)
+    assert rr <= 1e-12 and it < 100
+    r = dg.residual(u, MU_C0, None)
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(dg.residual(u_inf, MU_C0, None))
+    # the frozen pose is the t = 0 pose: same residual as the moving problem with zero velocities
+    mu0 = np.array([0.0, MU_C0[1], MU_C0[2]])     # h0 = 0: no heave velocity
+    assert np.allclose(dg.residual(u, mu0, None), r, atol=1e-15)
