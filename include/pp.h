@@ -88,6 +88,11 @@ typedef struct pp_config {
   int precision;
   int inner_maxit;    /* PP_PREC_MIXED: FP32 GMRES iterations per preconditioner application */
   double inner_rtol;  /* PP_PREC_MIXED: relative tolerance of that inner solve */
+  /* 0: the primal sweep keeps the stage linearization of the whole period in HBM.
+     K > 0: it keeps the state and Newton predictor every K steps and one K-step segment
+     of stage data; tangent / adjoint sweeps recompute each segment from its checkpoint
+     (identical iterates, so identical results) -- memory ~ Nt/K states + 3K stages. */
+  int checkpoint_stride;
 } pp_config;
 
 /* Fills *cfg with the paper's case (Sec. 6.1: gamma 1.4, Pr 0.72, Mach 0.2,

@@ -40,7 +40,7 @@ class pp_config(C.Structure):
                 ("lin_rtol", C.c_double), ("nk_gmres_rtol", C.c_double), ("nk_restart", C.c_int),
                 ("nk_max_newton", C.c_int), ("nk_max_krylov", C.c_int), ("adj_tol", C.c_double),
                 ("adj_restart", C.c_int), ("adj_maxit", C.c_int), ("precision", C.c_int),
-                ("inner_maxit", C.c_int), ("inner_rtol", C.c_double)]
+                ("inner_maxit", C.c_int), ("inner_rtol", C.c_double), ("checkpoint_stride", C.c_int)]
 
 
 class pp_shoot_stats(C.Structure):

@@ -104,6 +104,14 @@ struct pp_ctx {
   float* st_A32 = nullptr;
   float* st_AT32 = nullptr;
   std::vector<double> lin_qoi_rates;  // [Nt*3][2]
+  // checkpointed linearization (cfg.checkpoint_stride > 0): (u, predictor) at segment starts,
+  // one segment of stage data resident, slot = (step - seg_base)*3 + i
+  double* ck_u = nullptr;
+  double* ck_k = nullptr;
+  int seg_base = 0;
+  int seg_cur = -1;
+  size_t ck_segments = 0;
+  int64_t recomputed_segments = 0;
   double lin_W = 0.0, lin_Jx = 0.0;
   int64_t last_newton_iters = 0;
   int64_t last_gmres_iters = 0;

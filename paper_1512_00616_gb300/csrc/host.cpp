@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <utility>
 
@@ -284,7 +285,24 @@ int ensure_workspace(pp_ctx* ctx, const pp_mesh* mesh) {
 
 int ensure_store(pp_ctx* ctx, const pp_mesh* mesh, int Nt) {
   PP_TRY(ensure_workspace(ctx, mesh));
-  const size_t stages = (size_t)Nt * 3;
+  const int K = ctx->cfg.checkpoint_stride;
+  const size_t stages = (size_t)(K > 0 ? std::min(K, Nt) : Nt) * 3;
+  ctx->seg_cur = -1;
+  if (K > 0) {
+    const size_t nseg = (size_t)(Nt + K - 1) / K;
+    if (nseg > ctx->ck_segments || ctx->lin_mesh != mesh) {
+      cudaFree(ctx->ck_u);
+      cudaFree(ctx->ck_k);
+      ctx->ck_u = ctx->ck_k = nullptr;
+      ctx->ck_segments = 0;
+      if (cudaMalloc(&ctx->ck_u, sizeof(double) * nseg * mesh_nu(ctx, mesh)) != cudaSuccess ||
+          cudaMalloc(&ctx->ck_k, sizeof(double) * nseg * mesh_nu(ctx, mesh)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, PP_ENOMEM, "checkpoint storage does not fit in device memory");
+      }
+      ctx->ck_segments = nseg;
+    }
+  }
   if (ctx->store_stages >= stages && ctx->lin_mesh == mesh) return PP_OK;
   auto release = [&]() {
     for (double** p : {&ctx->st_J, &ctx->st_Ainv, &ctx->st_u, &ctx->st_JT, &ctx->st_AinvT}) {
@@ -368,6 +386,7 @@ void pp_config_default(pp_config* c) {
   c->adj_restart = 30;
   c->adj_maxit = 200;
   c->precision = PP_PREC_FP64;
+  c->checkpoint_stride = 0;
   c->inner_maxit = 30;
   c->inner_rtol = 1e-2;
 }
@@ -378,7 +397,8 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       cfg->nk_restart > 60 || cfg->adj_restart < 1 || cfg->adj_restart > 60 || !(cfg->T > 0) || !(cfg->Re > 0) ||
       !(cfg->Mach > 0) || (cfg->kin != PP_KIN_HEAVE_PITCH && cfg->kin != PP_KIN_FOURIER6) ||
       (cfg->precision != PP_PREC_FP64 && cfg->precision != PP_PREC_MIXED) ||
-      (cfg->precision == PP_PREC_MIXED && (cfg->inner_maxit < 1 || cfg->inner_maxit > 60)))
+      (cfg->precision == PP_PREC_MIXED && (cfg->inner_maxit < 1 || cfg->inner_maxit > 60)) ||
+      cfg->checkpoint_stride < 0)
     return PP_EINVAL;
   pp_ctx* ctx = new pp_ctx();
   ctx->cfg = *cfg;
@@ -480,6 +500,8 @@ int pp_destroy(pp_ctx* ctx) {
   cudaFree(ctx->st_JT32);
   cudaFree(ctx->st_A32);
   cudaFree(ctx->st_AT32);
+  cudaFree(ctx->ck_u);
+  cudaFree(ctx->ck_k);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return PP_OK;

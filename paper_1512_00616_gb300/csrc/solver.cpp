@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <functional>
 
 #include "context.h"
@@ -272,11 +273,11 @@ StageView stage_view_slot(pp_ctx* ctx, size_t s, double c) {
 }
 
 StageView stored_stage(pp_ctx* ctx, int n, int i) {
-  return stage_view_slot(ctx, (size_t)n * 3 + i, ctx->A[i][i] * ctx->cfg.T / ctx->lin_Nt);
+  return stage_view_slot(ctx, (size_t)(n - ctx->seg_base) * 3 + i, ctx->A[i][i] * ctx->cfg.T / ctx->lin_Nt);
 }
 
 const double* stored_u(pp_ctx* ctx, int n, int i) {
-  return ctx->st_u + ((size_t)n * 3 + i) * ctx->ws_nu;
+  return ctx->st_u + ((size_t)(n - ctx->seg_base) * 3 + i) * ctx->ws_nu;
 }
 
 // Everything a stage slot stores from the FP64 Jacobian in slot J (already assembled):
@@ -305,36 +306,28 @@ int finalize_stage_slot(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, b
 }  // namespace
 
 // --------------------------------------------------------------------------- primal sweep
-int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
-                 double* u_traj, double* u_final, double* qoi) {
-  PP_TRY(ensure_store(ctx, mesh, Nt));
-  ctx->lin_valid = false;
-  ctx->lin_mesh = mesh;
-  ctx->lin_mu.assign(mu, mu + n_mu);
-  ctx->lin_Nt = Nt;
+namespace {
+
+// DIRK steps [s0, s1) of a period of Nt steps from state u with Newton predictor kprev
+// (both updated in place).  Stage slot of (step, i) is (step - ctx->seg_base)*3 + i.
+// record: accumulate the QoI rates and write u_traj (off when a checkpointed segment is
+// recomputed).  The chord-Newton matrix restarts at s0, so a recomputation from a
+// checkpoint follows exactly the original iterates.
+int run_steps(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, double* u, double* kprev, int s0, int s1,
+              int Nt, bool record, double* u_traj) {
   const DevMesh& m = mesh->dev;
   const int64_t n = ctx->ws_nu;
   const double dt = ctx->cfg.T / Nt;
-  double* u = work_vec(ctx, 0);
   double* k[3] = {work_vec(ctx, 1), work_vec(ctx, 2), work_vec(ctx, 3)};
   double* base = work_vec(ctx, 4);
   double* r = work_vec(ctx, 5);
   double* R = work_vec(ctx, 6);
   double* dk = work_vec(ctx, 7);
-  double* kprev = work_vec(ctx, 8);
-  PP_TRY(copy(ctx, n, u, u0));
-  PP_CK(cudaMemsetAsync(kprev, 0, sizeof(double) * n, ctx->stream));
-  if (u_traj) PP_TRY(copy(ctx, n, u_traj, u));
-  ctx->lin_qoi_rates.assign((size_t)Nt * 6, 0.0);
-  double* d_rates = ctx->d_elem;  // reused below through colsum -> d_scalar
-  (void)d_rates;
-  ctx->last_newton_iters = 0;
-  ctx->last_gmres_iters = 0;
   // chord Newton: all stages share a_ii = gamma, so the stored matrix of the previous
   // stage (exact at its converged state) is the Newton matrix until contraction slows
   StageView nview{};
   bool have_nview = false;
-  for (int step = 0; step < Nt; ++step) {
+  for (int step = s0; step < s1; ++step) {
     const double t0 = step * dt;
     for (int i = 0; i < 3; ++i) {
       const double ti = t0 + ctx->c[i] * dt;
@@ -346,7 +339,8 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
       if (i == 1) PP_TRY(lincomb(ctx, n, base, {1.0, ctx->A[1][0]}, {u, k[0]}));
       if (i == 2) PP_TRY(lincomb(ctx, n, base, {1.0, ctx->A[2][0], ctx->A[2][1]}, {u, k[0], k[1]}));
       PP_TRY(copy(ctx, n, k[i], i == 0 ? kprev : k[i - 1]));
-      size_t slot = (size_t)step * 3 + i;
+      const size_t slot = (size_t)(step - ctx->seg_base) * 3 + i;
+      const size_t qslot = (size_t)step * 3 + i;
       const StageView sview = stage_view_slot(ctx, slot, c);
       double* Js = const_cast<double*>(sview.J);
       double* us = ctx->st_u + slot * n;
@@ -411,18 +405,77 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
         PP_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
         return set_error(ctx, PP_ENAN, "singular or non-finite stage block");
       }
+      if (!record) continue;
       // QoI rates at the converged stage
       PP_CK(launch_qoi(m, ctx->tb, ctx->ph, fr, us, ctx->d_elem, ctx->stream));
       PP_CK(launch_colsum(mesh->ne, 2, ctx->d_elem, ctx->d_scalar + 8, ctx->d_partial, ctx->d_counter, ctx->stream));
       PP_CK(cudaMemcpyAsync(ctx->h_scalar + 8, ctx->d_scalar + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                             ctx->stream));
       PP_CK(cudaStreamSynchronize(ctx->stream));
-      ctx->lin_qoi_rates[slot * 2] = ctx->h_scalar[8];
-      ctx->lin_qoi_rates[slot * 2 + 1] = ctx->h_scalar[9];
+      ctx->lin_qoi_rates[qslot * 2] = ctx->h_scalar[8];
+      ctx->lin_qoi_rates[qslot * 2 + 1] = ctx->h_scalar[9];
     }
     PP_TRY(lincomb(ctx, n, u, {1.0, ctx->b[0], ctx->b[1], ctx->b[2]}, {u, k[0], k[1], k[2]}));
     PP_TRY(copy(ctx, n, kprev, k[2]));
     if (u_traj) PP_TRY(copy(ctx, n, u_traj + (size_t)(step + 1) * n, u));
+  }
+  return PP_OK;
+}
+
+// Makes the stage data of step `step` resident (checkpointed linearization: recompute
+// its segment from the stored state and predictor at the segment start).
+int ensure_segment(pp_ctx* ctx, int step) {
+  const int K = ctx->cfg.checkpoint_stride;
+  if (K <= 0) return PP_OK;
+  const int seg = step / K;
+  if (seg == ctx->seg_cur) return PP_OK;
+  const int64_t n = ctx->ws_nu;
+  double* u = work_vec(ctx, 0);
+  double* kprev = work_vec(ctx, 8);
+  PP_TRY(copy(ctx, n, u, ctx->ck_u + (size_t)seg * n));
+  PP_TRY(copy(ctx, n, kprev, ctx->ck_k + (size_t)seg * n));
+  ctx->seg_base = seg * K;
+  const int s1 = std::min((seg + 1) * K, ctx->lin_Nt);
+  PP_TRY(run_steps(ctx, ctx->lin_mesh, ctx->lin_mu.data(), (int)ctx->lin_mu.size(), u, kprev, seg * K, s1,
+                   ctx->lin_Nt, false, nullptr));
+  ctx->seg_cur = seg;
+  ctx->recomputed_segments++;
+  return PP_OK;
+}
+
+}  // namespace
+
+int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                 double* u_traj, double* u_final, double* qoi) {
+  PP_TRY(ensure_store(ctx, mesh, Nt));
+  ctx->lin_valid = false;
+  ctx->lin_mesh = mesh;
+  ctx->lin_mu.assign(mu, mu + n_mu);
+  ctx->lin_Nt = Nt;
+  const int64_t n = ctx->ws_nu;
+  const double dt = ctx->cfg.T / Nt;
+  double* u = work_vec(ctx, 0);
+  double* kprev = work_vec(ctx, 8);
+  PP_TRY(copy(ctx, n, u, u0));
+  PP_CK(cudaMemsetAsync(kprev, 0, sizeof(double) * n, ctx->stream));
+  if (u_traj) PP_TRY(copy(ctx, n, u_traj, u));
+  ctx->lin_qoi_rates.assign((size_t)Nt * 6, 0.0);
+  ctx->last_newton_iters = 0;
+  ctx->last_gmres_iters = 0;
+  const int K = ctx->cfg.checkpoint_stride;
+  if (K <= 0) {
+    ctx->seg_base = 0;
+    PP_TRY(run_steps(ctx, mesh, mu, n_mu, u, kprev, 0, Nt, Nt, true, u_traj));
+  } else {
+    // store (u, predictor) at every K-th step; keep one segment of stage data resident
+    const int nseg = (Nt + K - 1) / K;
+    for (int seg = 0; seg < nseg; ++seg) {
+      PP_TRY(copy(ctx, n, ctx->ck_u + (size_t)seg * n, u));
+      PP_TRY(copy(ctx, n, ctx->ck_k + (size_t)seg * n, kprev));
+      ctx->seg_base = seg * K;
+      PP_TRY(run_steps(ctx, mesh, mu, n_mu, u, kprev, seg * K, std::min((seg + 1) * K, Nt), Nt, true, u_traj));
+      ctx->seg_cur = seg;
+    }
   }
   double W = 0.0, Jx = 0.0;
   for (int step = 0; step < Nt; ++step)
@@ -460,6 +513,7 @@ int tangent_sweep(pp_ctx* ctx, const double* v, double* out) {
   PP_TRY(copy(ctx, n, du, v));
   ctx->last_gmres_tangent = 0;
   for (int step = 0; step < Nt; ++step) {
+    PP_TRY(ensure_segment(ctx, step));
     for (int i = 0; i < 3; ++i) {
       StageView sv = stored_stage(ctx, step, i);
       const double* win = du;
@@ -503,6 +557,7 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
   PP_TRY(copy(ctx, n, lam, lam_Nt));
   ctx->last_gmres_adjoint = 0;
   for (int step = Nt - 1; step >= 0; --step) {
+    PP_TRY(ensure_segment(ctx, step));
     for (int i = 2; i >= 0; --i) {
       StageView sv = stored_stage(ctx, step, i);
       const double ti = step * dt + ctx->c[i] * dt;
