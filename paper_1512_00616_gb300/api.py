@@ -27,6 +27,9 @@ EXPORTED = [
     "pp_steady_state",
     # include/pp_prof.h
     "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
+    # include/pp_learn.h
+    "pp_gemm_f32", "pp_gemm_f64", "pp_bias_act_f32", "pp_gelu_backward_f32", "pp_colsum_f32", "pp_mse_f32",
+    "pp_adam_f32", "pp_syevj_f64",
 ]
 PP_K = dict(none=0, jacobian=1, residual=2, stage_matvec=3, block_apply=4, block_inverse=5, krylov=6, other=7,
             stage_matvec32=8, block_apply32=9, krylov32=10)
@@ -89,6 +92,14 @@ def _load():
         "pp_prof_counts": (I, [C.POINTER(C.c_int64)]),
         "pp_measure_fp64_peak": (I, [I, dp]),
         "pp_sweep_counts": (I, [P] + [C.POINTER(C.c_int64)] * 4),
+        "pp_gemm_f32": (I, [I, I, I, C.c_float, P, I, I, P, I, I, C.c_float, P, I, P]),
+        "pp_gemm_f64": (I, [I, I, I, D, P, I, I, P, I, I, D, P, I, P]),
+        "pp_bias_act_f32": (I, [I, I, P, P, P, I, P]),
+        "pp_gelu_backward_f32": (I, [I, P, P, P, P]),
+        "pp_colsum_f32": (I, [I, I, P, P, P]),
+        "pp_mse_f32": (I, [I, P, P, P, P, P]),
+        "pp_adam_f32": (I, [I, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I, P]),
+        "pp_syevj_f64": (I, [I, P, P, P, D, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -287,3 +298,56 @@ def pp_sweep_counts(ctx):
     v = [C.c_int64() for _ in range(4)]
     _check(ctx, _lib.pp_sweep_counts(ctx, *[C.byref(x) for x in v]))
     return dict(newton=v[0].value, gmres_primal=v[1].value, gmres_tangent=v[2].value, gmres_adjoint=v[3].value)
+
+
+# --------------------------------------------------------------------------- learned warm start (include/pp_learn.h)
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _lcheck(code, name):
+    if code != 0:
+        raise PPError(code, name)
+
+
+def pp_gemm(A, B, C_out, ta=False, tb=False, alpha=1.0, beta=0.0):
+    """C_out = alpha op(A) op(B) + beta C_out (row-major torch CUDA tensors, float32 or float64)."""
+    import torch
+    m = A.shape[1] if ta else A.shape[0]
+    k = A.shape[0] if ta else A.shape[1]
+    n = B.shape[0] if tb else B.shape[1]
+    f = _lib.pp_gemm_f32 if A.dtype == torch.float32 else _lib.pp_gemm_f64
+    _lcheck(f(m, n, k, alpha, _ptr(A), A.shape[1], int(ta), _ptr(B), B.shape[1], int(tb), beta, _ptr(C_out),
+              C_out.shape[1], _stream()), "pp_gemm")
+
+
+def pp_bias_act_f32(Z, b, H, gelu_on):
+    _lcheck(_lib.pp_bias_act_f32(Z.shape[0], Z.shape[1], _ptr(Z), _ptr(b), _ptr(H), int(gelu_on), _stream()),
+            "pp_bias_act_f32")
+
+
+def pp_gelu_backward_f32(Z, dH, dZ):
+    _lcheck(_lib.pp_gelu_backward_f32(Z.numel(), _ptr(Z), _ptr(dH), _ptr(dZ), _stream()), "pp_gelu_backward_f32")
+
+
+def pp_colsum_f32(dZ, db):
+    _lcheck(_lib.pp_colsum_f32(dZ.shape[0], dZ.shape[1], _ptr(dZ), _ptr(db), _stream()), "pp_colsum_f32")
+
+
+def pp_mse_f32(Y, T, dY, loss):
+    _lcheck(_lib.pp_mse_f32(Y.numel(), _ptr(Y), _ptr(T), _ptr(dY), _ptr(loss), _stream()), "pp_mse_f32")
+
+
+def pp_adam_f32(w, g, m1, m2, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    _lcheck(_lib.pp_adam_f32(w.numel(), _ptr(w), _ptr(g), _ptr(m1), _ptr(m2), lr, b1, b2, eps, int(step),
+                             _stream()), "pp_adam_f32")
+
+
+def pp_syevj_f64(A, V, w, tol=1e-14, max_sweeps=30):
+    _lcheck(_lib.pp_syevj_f64(A.shape[0], _ptr(A), _ptr(V), _ptr(w), tol, max_sweeps, None, _stream()),
+            "pp_syevj_f64")
