@@ -258,7 +258,7 @@ int ensure_workspace(pp_ctx* ctx, const pp_mesh* mesh) {
   cudaFree(ctx->d_elem);
   ctx->d_J = ctx->d_Ainv = ctx->d_vec = ctx->d_elem = nullptr;
   const size_t nb2 = (size_t)ctx->tb.nb * ctx->tb.nb;
-  ctx->n_vec = 24;
+  ctx->n_vec = 27;  // 0-8 primal, 9-15 tangent, 14-23 adjoint, 24-26 shooting / periodic adjoint
   if (cudaMalloc(&ctx->d_J, sizeof(double) * mesh->ne * 4 * nb2) != cudaSuccess ||
       cudaMalloc(&ctx->d_Ainv, sizeof(double) * mesh->ne * nb2) != cudaSuccess ||
       cudaMalloc(&ctx->d_vec, sizeof(double) * ctx->n_vec * nu) != cudaSuccess ||

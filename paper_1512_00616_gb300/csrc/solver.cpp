@@ -741,7 +741,7 @@ int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const
     PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0_out, Nt, nullptr, uN, qoi));
     st.primal_sweeps++;
     st.stage_newton_iters += ctx->last_newton_iters;
-    double* R = work_vec(ctx, 4);  // primal-sweep scratch, free now
+    double* R = work_vec(ctx, 24);  // outer-level vectors (24..26) are never touched by the sweeps
     PP_TRY(lincomb(ctx, n, R, {1.0, -1.0}, {uN, u0_out}));
     double rn;
     PP_TRY(host_norm(ctx, n, R, &rn));
@@ -753,9 +753,9 @@ int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const
     }
     if (it == ctx->cfg.nk_max_newton) break;
     // (Phi - I) du = R with matvec (Phi - I) v = -(v - Phi v)
-    double* Rsave = work_vec(ctx, 5);
+    double* Rsave = work_vec(ctx, 25);
     PP_TRY(copy(ctx, n, Rsave, R));
-    double* du = work_vec(ctx, 6);
+    double* du = work_vec(ctx, 26);
     Op A = [&](const double* in, double* out) {
       PP_TRY(tangent_sweep(ctx, in, out));
       PP_TRY(lincomb(ctx, n, out, {-1.0}, {out}));
@@ -788,9 +788,9 @@ int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_m
   }
   const int64_t n = ctx->ws_nu;
   Krylov& K = ctx->kout;
-  double* d = work_vec(ctx, 4);
-  double* x = work_vec(ctx, 5);
-  double* z = work_vec(ctx, 6);
+  double* d = work_vec(ctx, 24);  // outer-level vectors (24..26) are never touched by the sweeps
+  double* x = work_vec(ctx, 25);
+  double* z = work_vec(ctx, 26);
   PP_CK(cudaMemsetAsync(z, 0, sizeof(double) * n, ctx->stream));
   // d = lambda^(0)(0) with the QoI terms; solve (Phi^T - I) x = -d
   PP_TRY(adjoint_sweep(ctx, z, weights, d, nullptr));

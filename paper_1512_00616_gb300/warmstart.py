@@ -205,46 +205,65 @@ def lhs(n, lo, hi, seed):
     return lo + u * (hi - lo)
 
 
-def experiment(config="c0", n_train=96, n_test=16, tol=1e-8, epochs=3000, seed=44, mixed=False):
+def experiment(config="c0", n_train=96, n_test=16, tol=1e-8, epochs=3000, seed=44):
+    """Data generation with the GPU shooter, POD + network training, then per held-out mu
+    the time to a periodic gradient (u0 with ||R|| <= tol, then the periodic adjoint for
+    J_E) by (a) plain FP64 from the steady-state cold start and (b) mixed precision from
+    the learned warm start."""
     from pp_inputs import CONFIGS, KIN_FOURIER6, MU_F6_BASE, MU_F6_SCALE, config_mesh
     c = CONFIGS[config]
     mesh = config_mesh(config)
-    cfg = A.pp_config_default(p=c["p"], kin=KIN_FOURIER6, precision=A.PP_PREC_MIXED if mixed else A.PP_PREC_FP64)
-    ctx = A.pp_create(cfg)
-    m = A.pp_mesh_create(ctx, mesh.verts, mesh.tris, mesh.ftag)
+    T = 5.0
+    ctxs, meshes = {}, {}
+    for name, prec in (("fp64", A.PP_PREC_FP64), ("mixed", A.PP_PREC_MIXED)):
+        ctxs[name] = A.pp_create(A.pp_config_default(p=c["p"], kin=KIN_FOURIER6, precision=prec, adj_tol=1e-10))
+        meshes[name] = A.pp_mesh_create(ctxs[name], mesh.verts, mesh.tris, mesh.ftag)
     lo, hi = MU_F6_BASE - 0.2 * MU_F6_SCALE, MU_F6_BASE + 0.2 * MU_F6_SCALE
     train = lhs(n_train, lo, hi, seed)
     test = lhs(n_test, lo, hi, seed + 1)
-    nu = A.pp_mesh_info(m)[2]
-    # data generation: continuation from the previous periodic state
+    nu = A.pp_mesh_info(meshes["mixed"])[2]
+    # data generation (mixed precision, continuation from the previous periodic state)
     U = torch.empty(n_train, nu, dtype=torch.float64, device="cuda")
     prev = None
     t0 = time.perf_counter()
-    order = np.argsort(train[:, 0])
-    for i in order:
+    for i in np.argsort(train[:, 0]):
         u0 = torch.empty(nu, dtype=torch.float64, device="cuda")
-        A.pp_shoot_nk(ctx, m, train[i], c["Nt"], 1e-10, u0, u0_guess=prev)
+        A.pp_shoot_nk(ctxs["mixed"], meshes["mixed"], train[i], c["Nt"], 1e-10, u0, u0_guess=prev)
         U[i] = u0
         prev = u0
+    torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     ws = LearnedWarmStart(n_modes=64).fit(train, U, epochs=epochs)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    w = np.array([-1.0 / T, 0.0])  # F = J_E
     rows = []
     for mu in test:
-        _, _, st_c, _, t_c = shoot_with_warm_start(ctx, m, mu, c["Nt"], tol)
-        _, _, st_l, used, t_l = shoot_with_warm_start(ctx, m, mu, c["Nt"], tol, predictor=ws)
-        rows.append(dict(cold_newton=st_c["newton_iters"], cold_krylov=st_c["krylov_iters"], cold_s=t_c,
-                         learned_newton=st_l["newton_iters"], learned_krylov=st_l["krylov_iters"], learned_s=t_l,
-                         used=used, first_residual_learned=st_l["residual"][0],
-                         first_residual_cold=st_c["residual"][0]))
-    A.pp_mesh_destroy(m)
-    A.pp_destroy(ctx)
+        # (a) plain FP64, cold start
+        t0 = time.perf_counter()
+        _, _, st_a, _, _ = shoot_with_warm_start(ctxs["fp64"], meshes["fp64"], mu, c["Nt"], tol)
+        _, g_a, _ = A.pp_periodic_adjoint(ctxs["fp64"], meshes["fp64"], mu, c["Nt"], w)
+        t_a = time.perf_counter() - t0
+        # (b) mixed precision, learned warm start
+        t0 = time.perf_counter()
+        _, _, st_b, used, _ = shoot_with_warm_start(ctxs["mixed"], meshes["mixed"], mu, c["Nt"], tol, predictor=ws)
+        _, g_b, _ = A.pp_periodic_adjoint(ctxs["mixed"], meshes["mixed"], mu, c["Nt"], w)
+        t_b = time.perf_counter() - t0
+        rows.append(dict(plain_newton=st_a["newton_iters"], plain_tangent_sweeps=st_a["krylov_iters"],
+                         plain_s=t_a, learned_newton=st_b["newton_iters"],
+                         learned_tangent_sweeps=st_b["krylov_iters"], learned_s=t_b,
+                         first_residual_plain=st_a["residual"][0], first_residual_learned=st_b["residual"][0],
+                         grad_rel_diff=float(np.linalg.norm(g_b - g_a) / np.linalg.norm(g_a)), used=used))
+    for name in ctxs:
+        A.pp_mesh_destroy(meshes[name])
+        A.pp_destroy(ctxs[name])
     agg = {k: float(np.mean([r[k] for r in rows])) for k in rows[0] if k != "used"}
+    agg["grad_rel_diff_max"] = float(np.max([r["grad_rel_diff"] for r in rows]))
     return dict(config=config, n_train=n_train, n_test=n_test, tol=tol, data_s=t_data, train_s=t_train,
-                final_loss=ws.losses[-1], pod_energy_64=float(ws.pod.energy.sum()),
-                fallbacks=sum(r["used"] != "learned" for r in rows), mean=agg)
+                final_loss=ws.losses[-1], pod_modes=int(ws.pod.modes.shape[0]),
+                pod_energy=float(ws.pod.energy.sum()), fallbacks=sum(r["used"] != "learned" for r in rows),
+                mean=agg)
 
 
 def main():
@@ -253,9 +272,8 @@ def main():
     ap.add_argument("--train", type=int, default=96)
     ap.add_argument("--test", type=int, default=16)
     ap.add_argument("--epochs", type=int, default=3000)
-    ap.add_argument("--mixed", action="store_true")
     a = ap.parse_args()
-    print(json.dumps(experiment(a.config, a.train, a.test, epochs=a.epochs, mixed=a.mixed)))
+    print(json.dumps(experiment(a.config, a.train, a.test, epochs=a.epochs)))
 
 
 if __name__ == "__main__":

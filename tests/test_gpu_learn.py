@@ -61,5 +61,7 @@ def test_learned_warm_start_beats_cold_start():
     r = experiment("tiny", n_train=16, n_test=3, tol=1e-8, epochs=1500)
     print(r)
     assert r["fallbacks"] == 0
-    assert r["mean"]["learned_newton"] < r["mean"]["cold_newton"]
-    assert r["mean"]["first_residual_learned"] < r["mean"]["first_residual_cold"]
+    assert r["mean"]["learned_newton"] < r["mean"]["plain_newton"]
+    assert r["mean"]["first_residual_learned"] < r["mean"]["first_residual_plain"]
+    # both paths reach the same periodic gradient (1e-6 accuracy target)
+    assert r["mean"]["grad_rel_diff_max"] <= 1e-6
