@@ -58,7 +58,7 @@ def test_jacobi_eigensolver_and_pod():
 
 def test_learned_warm_start_beats_cold_start():
     from paper_1512_00616_gb300.warmstart import experiment
-    r = experiment("tiny", n_train=16, n_test=3, tol=1e-8, epochs=1500)
+    r = experiment("tiny", n_train=24, n_test=3, tol=1e-8, epochs=4000)
     print(r)
     assert r["fallbacks"] == 0
     assert r["mean"]["learned_newton"] < r["mean"]["plain_newton"]
