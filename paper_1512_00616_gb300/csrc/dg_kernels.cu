@@ -159,15 +159,47 @@ __global__ void __launch_bounds__(RES_WARPS * 32)
 }
 
 // ------------------------------------------------------------------------ Jacobian
+// Shared-memory carve-up of k_jacobian (doubles), sized from the runtime degree.
+struct JacSmem {
+  int su, Cv, Cf, Tv, Tf, Tn, Wv, Wf, Wn, total;
+  __host__ __device__ JacSmem(int nb, int Np, int nqv) {
+    su = 0;
+    Cv = su + 4 * nb;
+    Cf = Cv + nqv * 4 * 2 * NSV;
+    Tv = Cf + 3 * kMaxQf * 4 * NSF;
+    Tf = Tv + nqv * 3 * Np;
+    Tn = Tf + 3 * kMaxQf * 3 * Np;
+    Wv = Tn + 3 * kMaxQf * 3 * Np;
+    Wf = Wv + nqv * 2 * Np;
+    Wn = Wf + 3 * kMaxQf * Np;
+    total = Wn + 3 * kMaxQf * Np;
+  }
+};
+
+// Element block Jacobian.  Phase 1: exact derivatives of the quadrature-point fluxes
+// with respect to (U, grad U) by dual numbers (12 seeds per volume point, 24 per face
+// point: both traces), weighted and projected on the reference test gradients (C).
+// Phase 2, per variable pair (a, b): W = sum over trial types (value, d/dx, d/dy) of
+// C * T (T = trial basis values and physical gradients at the points), then
+// J_ab = D W with D the test basis (gradients for the volume, values on faces) -- a
+// small GEMM-shaped contraction instead of re-evaluating trial gradients per entry.
 __global__ void __launch_bounds__(JAC_THREADS)
     k_jacobian(DevMesh m, DevTables tb, Phys ph, FrameT<double> fr, const double* __restrict__ u,
                double* __restrict__ J) {
-  __shared__ double su[4 * kMaxNb];
-  __shared__ double Cv[kMaxQv * 4 * 2 * NSV];
-  __shared__ double Cf[3 * kMaxQf * 4 * NSF];
+  extern __shared__ double smem[];
   const int e = blockIdx.x;
   const int tid = threadIdx.x;
   const int Np = tb.Np, nb = tb.nb, nqv = tb.nqv, nqf = tb.nqf;
+  const JacSmem L(nb, Np, nqv);
+  double* su = smem + L.su;
+  double* Cv = smem + L.Cv;
+  double* Cf = smem + L.Cf;
+  double* Tv = smem + L.Tv;  // [q][t][j]
+  double* Tf = smem + L.Tf;  // [f][q][t][j] (own trace)
+  double* Tn = smem + L.Tn;  // [f][q][t][j] (neighbour trace at the matched point)
+  double* Wv = smem + L.Wv;  // [q][k][j]
+  double* Wf = smem + L.Wf;  // [f][q][j]
+  double* Wn = smem + L.Wn;  // [f][q][j]
   for (int idx = tid; idx < 4 * nb; idx += JAC_THREADS) {
     int slot = idx / nb, k = idx - slot * nb;
     int src = e;
@@ -189,7 +221,7 @@ __global__ void __launch_bounds__(JAC_THREADS)
   }
   frd.hd = Dual(fr.hd);
 
-  // volume: derivative of the weighted, test-gradient-projected flux per seed
+  // phase 1a: volume seeds
   for (int task = tid; task < nqv * NSV; task += JAC_THREADS) {
     int q = task / NSV, s = task - q * NSV;
     double U0[4], dU0[4][2];
@@ -212,7 +244,7 @@ __global__ void __launch_bounds__(JAC_THREADS)
       Cv[((q * 4 + a) * 2 + 1) * NSV + s] = wq * (P[1] * F[a][0].d + P[3] * F[a][1].d);
     }
   }
-  // faces
+  // phase 1b: face seeds
   for (int task = tid; task < 3 * nqf * NSF; task += JAC_THREADS) {
     int f = task / (nqf * NSF);
     int rem = task - f * nqf * NSF;
@@ -259,65 +291,79 @@ __global__ void __launch_bounds__(JAC_THREADS)
 #pragma unroll
     for (int a = 0; a < 4; ++a) out[a * NSF] = wl * H[a].d;
   }
+  // trial tables: basis values and physical gradients at the volume / face points
+  for (int idx = tid; idx < nqv * Np; idx += JAC_THREADS) {
+    const int q = idx / Np, j = idx - q * Np;
+    const double* dj = tb.dphi_v + 2 * (q * Np + j);
+    Tv[(q * 3 + 0) * Np + j] = tb.phi_v[q * Np + j];
+    Tv[(q * 3 + 1) * Np + j] = P[0] * dj[0] + P[1] * dj[1];
+    Tv[(q * 3 + 2) * Np + j] = P[2] * dj[0] + P[3] * dj[1];
+  }
+  for (int idx = tid; idx < 3 * nqf * Np; idx += JAC_THREADS) {
+    const int f = idx / (nqf * Np), rem = idx - f * nqf * Np, q = rem / Np, j = rem - q * Np;
+    const double* dj = tb.dphi_f + 2 * ((f * nqf + q) * Np + j);
+    double* to = Tf + ((f * kMaxQf + q) * 3) * Np + j;
+    to[0] = tb.phi_f[(f * nqf + q) * Np + j];
+    to[Np] = P[0] * dj[0] + P[1] * dj[1];
+    to[2 * Np] = P[2] * dj[0] + P[3] * dj[1];
+    double* tn = Tn + ((f * kMaxQf + q) * 3) * Np + j;
+    if (m.tag[3 * e + f] == 0) {
+      const int e2 = m.nbr[3 * e + f], g = m.nbrface[3 * e + f], qq = nqf - 1 - q;
+      double P2[4];
+      frame_P(fr, m.BinvT + 4 * e2, P2);
+      const double* dn = tb.dphi_f + 2 * ((g * nqf + qq) * Np + j);
+      tn[0] = tb.phi_f[(g * nqf + qq) * Np + j];
+      tn[Np] = P2[0] * dn[0] + P2[1] * dn[1];
+      tn[2 * Np] = P2[2] * dn[0] + P2[3] * dn[1];
+    } else {
+      tn[0] = tn[Np] = tn[2 * Np] = 0.0;
+    }
+  }
   __syncthreads();
 
+  // phase 2: per variable pair (a, b)
   const size_t nb2 = (size_t)nb * nb;
   double* Jd = J + (size_t)e * 4 * nb2;
-  for (int ent = tid; ent < nb * nb; ent += JAC_THREADS) {
-    int col = ent / nb, row = ent - col * nb;
-    int a = row / Np, i = row - a * Np, b = col / Np, j = col - b * Np;
-    double acc = 0.0;
-    for (int q = 0; q < nqv; ++q) {
-      const double* di = tb.dphi_v + 2 * (q * Np + i);
-      const double* dj = tb.dphi_v + 2 * (q * Np + j);
-      double phij = tb.phi_v[q * Np + j];
-      double g0 = P[0] * dj[0] + P[1] * dj[1];
-      double g1 = P[2] * dj[0] + P[3] * dj[1];
-      const double* C0 = Cv + ((q * 4 + a) * 2) * NSV;
-      const double* C1 = C0 + NSV;
-      double t0 = C0[b] * phij + C0[4 + 2 * b] * g0 + C0[5 + 2 * b] * g1;
-      double t1 = C1[b] * phij + C1[4 + 2 * b] * g0 + C1[5 + 2 * b] * g1;
-      acc += di[0] * t0 + di[1] * t1;
-    }
-    for (int f = 0; f < 3; ++f) {
-      for (int q = 0; q < nqf; ++q) {
-        const double* dj = tb.dphi_f + 2 * ((f * nqf + q) * Np + j);
-        double phii = tb.phi_f[(f * nqf + q) * Np + i];
-        double phij = tb.phi_f[(f * nqf + q) * Np + j];
-        double g0 = P[0] * dj[0] + P[1] * dj[1];
-        double g1 = P[2] * dj[0] + P[3] * dj[1];
-        const double* C = Cf + ((f * kMaxQf + q) * 4 + a) * NSF;
-        acc -= phii * (C[b] * phij + C[4 + 2 * b] * g0 + C[5 + 2 * b] * g1);
+  const int nW = nqv * 2 * Np, nWf = 3 * nqf * Np;
+  for (int ab = 0; ab < 16; ++ab) {
+    const int a = ab >> 2, b = ab & 3;
+    const int sb[3] = {b, 4 + 2 * b, 5 + 2 * b};
+    for (int idx = tid; idx < nW + 2 * nWf; idx += JAC_THREADS) {
+      if (idx < nW) {
+        const int q = idx / (2 * Np), rem = idx - q * 2 * Np, k = rem / Np, j = rem - k * Np;
+        const double* C = Cv + ((q * 4 + a) * 2 + k) * NSV;
+        const double* T = Tv + (q * 3) * Np + j;
+        Wv[idx] = C[sb[0]] * T[0] + C[sb[1]] * T[Np] + C[sb[2]] * T[2 * Np];
+      } else {
+        const int id2 = idx - nW;
+        const int side = id2 >= nWf;  // 0 own trace, 1 neighbour trace
+        const int id3 = side ? id2 - nWf : id2;
+        const int f = id3 / (nqf * Np), rem = id3 - f * nqf * Np, q = rem / Np, j = rem - q * Np;
+        const double* C = Cf + ((f * kMaxQf + q) * 4 + a) * NSF + (side ? 12 : 0);
+        const double* T = (side ? Tn : Tf) + ((f * kMaxQf + q) * 3) * Np + j;
+        const double w = C[sb[0]] * T[0] + C[sb[1]] * T[Np] + C[sb[2]] * T[2 * Np];
+        (side ? Wn : Wf)[(f * kMaxQf + q) * Np + j] = w;
       }
     }
-    Jd[(size_t)col * nb + row] = acc;
-  }
-  for (int f = 0; f < 3; ++f) {
-    double* Jf = Jd + (size_t)(1 + f) * nb2;
-    int tag = m.tag[3 * e + f];
-    if (tag != 0) {
-      for (int ent = tid; ent < nb * nb; ent += JAC_THREADS) Jf[ent] = 0.0;
-      continue;
-    }
-    int e2 = m.nbr[3 * e + f], g = m.nbrface[3 * e + f];
-    double P2[4];
-    frame_P(fr, m.BinvT + 4 * e2, P2);
-    for (int ent = tid; ent < nb * nb; ent += JAC_THREADS) {
-      int col = ent / nb, row = ent - col * nb;
-      int a = row / Np, i = row - a * Np, b = col / Np, j = col - b * Np;
+    __syncthreads();
+    for (int idx = tid; idx < 4 * Np * Np; idx += JAC_THREADS) {
+      const int slot = idx / (Np * Np), rem = idx - slot * Np * Np, j = rem / Np, i = rem - j * Np;
       double acc = 0.0;
-      for (int q = 0; q < nqf; ++q) {
-        int qq = nqf - 1 - q;
-        const double* dj = tb.dphi_f + 2 * ((g * nqf + qq) * Np + j);
-        double phii = tb.phi_f[(f * nqf + q) * Np + i];
-        double phij = tb.phi_f[(g * nqf + qq) * Np + j];
-        double g0 = P2[0] * dj[0] + P2[1] * dj[1];
-        double g1 = P2[2] * dj[0] + P2[3] * dj[1];
-        const double* C = Cf + ((f * kMaxQf + q) * 4 + a) * NSF;
-        acc -= phii * (C[12 + b] * phij + C[16 + 2 * b] * g0 + C[17 + 2 * b] * g1);
+      if (slot == 0) {
+        for (int q = 0; q < nqv; ++q) {
+          const double* di = tb.dphi_v + 2 * (q * Np + i);
+          acc += di[0] * Wv[(q * 2 + 0) * Np + j] + di[1] * Wv[(q * 2 + 1) * Np + j];
+        }
+        for (int f = 0; f < 3; ++f)
+          for (int q = 0; q < nqf; ++q)
+            acc -= tb.phi_f[(f * nqf + q) * Np + i] * Wf[(f * kMaxQf + q) * Np + j];
+      } else {
+        const int f = slot - 1;
+        for (int q = 0; q < nqf; ++q) acc -= tb.phi_f[(f * nqf + q) * Np + i] * Wn[(f * kMaxQf + q) * Np + j];
       }
-      Jf[(size_t)col * nb + row] = acc;
+      Jd[(size_t)slot * nb2 + (size_t)(b * Np + j) * nb + a * Np + i] = acc;
     }
+    __syncthreads();
   }
 }
 
@@ -453,7 +499,14 @@ cudaError_t launch_residual_dframe(const DevMesh& m, const DevTables& tb, const 
 cudaError_t launch_jacobian(const DevMesh& m, const DevTables& tb, const Phys& ph, const FrameT<double>& fr,
                             const double* u, double* J, cudaStream_t st) {
   ProfScope ps(PP_K_JACOBIAN, st);
-  k_jacobian<<<m.ne, JAC_THREADS, 0, st>>>(m, tb, ph, fr, u, J);
+  const size_t bytes = sizeof(double) * JacSmem(tb.nb, tb.Np, tb.nqv).total;
+  static size_t configured = 0;
+  if (bytes > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = bytes;
+  }
+  k_jacobian<<<m.ne, JAC_THREADS, bytes, st>>>(m, tb, ph, fr, u, J);
   return cudaGetLastError();
 }
 
