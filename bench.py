@@ -36,7 +36,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c1")
-    ap.add_argument("--roofline-kernel", default="stage_matvec")
+    ap.add_argument("--roofline-kernel", default=None,
+                    help="kernel class for the roofline (default: stage_op in fp64, stage_matvec32 in mixed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -235,17 +236,23 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c):
         return None
     t = res["kern_ms"] / res["kern_launches"] * 1e-3
     if kernel == "jacobian":
-        # contraction: per diagonal entry 2 k x 3 trial terms per volume point + 3 per face point,
-        # per off-diagonal entry 3 per face point (2 flops each)
-        flops = ne * (nb * nb * (2 * nqv * 8 + 3 * nqf * 6) + 3 * nb * nb * nqf * 6)
+        # basis contraction per variable pair (16 per element): W = C T over 3 trial types at
+        # 2 nqv Np volume and 2 x 3 nqf Np face entries, then J_ab = D W (Np^2 (2 nqv + 3 nqf)
+        # for the diagonal block, Np^2 nqf for each face block); 2 flops per FMA.  The dual-
+        # number flux derivatives are not counted.
+        w_fma = 3 * (2 * nqv * Np + 2 * 3 * nqf * Np)
+        j_fma = Np * Np * (2 * nqv + 3 * nqf) + 3 * Np * Np * nqf
+        flops = ne * 16 * 2 * (w_fma + j_fma)
         ach = flops / t / 1e12
         return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
                 "frac": ach / fp64_tflops if fp64_tflops else None, "traffic": None,
                 "kernel": "k_jacobian", "launches": res["kern_launches"], "avg_us": t * 1e6}
-    if kernel in ("stage_matvec", "block_apply", "stage_matvec32", "block_apply32"):
-        blocks = 4 if kernel.startswith("stage_matvec") else 1
+    if kernel in ("stage_matvec", "block_apply", "stage_matvec32", "block_apply32", "stage_op", "stage_op32"):
+        blocks = 4 if kernel.startswith("stage_matvec") else (3 if kernel.startswith("stage_op") else 1)
         word = 4 if kernel.endswith("32") else 8
-        byts = ne * (blocks * nb * nb * word + 2 * nb * word)
+        # matrix blocks + input slices + output (stage_op: 3 neighbour slices, the element's own
+        # slice for the identity term and the output)
+        byts = ne * (blocks * nb * nb * word + (5 if kernel.startswith("stage_op") else 2) * nb * word)
         if word == 8:
             # GB300 issues ~2 FP64 FMA per clock per SM: the FP64 block product is FP64-ALU bound
             # (its FMA floor exceeds its HBM floor), so it is held against the measured FP64 peak
@@ -253,17 +260,22 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c):
             ach = flops / t / 1e12
             return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
                     "frac": ach / fp64_tflops if fp64_tflops else None, "traffic": None,
-                    "kernel": "k_" + kernel.replace("32", "") + "<double>", "launches": res["kern_launches"],
+                    "kernel": ("k_stream_rows<%d,3,double> (I + B, folded block-Jacobi)" % nb if kernel == "stage_op"
+                               else "k_" + kernel.replace("32", "") + "<double>"), "launches": res["kern_launches"],
                     "avg_us": t * 1e6, "hbm_gbs_equiv": byts / t / 1e9}
         ach = byts / t / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "k_" + kernel.replace("32", "") + "<float>",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": ("k_stream_rows<%d,3,float> (I + B, folded block-Jacobi)" % nb if kernel == "stage_op32"
+                           else "k_" + kernel.replace("32", "") + "<float>"),
                 "launches": res["kern_launches"], "avg_us": t * 1e6}
     return None
 
 
 def main():
     args = parse()
+    if args.roofline_kernel is None:
+        args.roofline_kernel = "stage_op32" if args.precision == "mixed" else "stage_op"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -66,7 +66,9 @@ typedef struct pp_config {
   double T;           /* period of the motion (5) */
   int kin;            /* PP_KIN_* */
   int device;         /* CUDA device ordinal */
-  void* stream;       /* cudaStream_t to issue work on; NULL = the library's own stream */
+  void* stream;       /* cudaStream_t to issue work on; NULL = the library's own non-blocking
+                         stream, which does not wait for work on other streams (including the
+                         legacy default stream): device inputs must be complete before a call */
   /* primal stage solves (Newton with GMRES, block-Jacobi preconditioned) */
   double newton_tol;  /* stop when ||dk||_2 <= newton_tol * max(1, ||u_i||_2) */
   int newton_maxit;

@@ -24,7 +24,10 @@ extern "C" {
 #define PP_K_STAGE_MATVEC32 8  /* FP32 block-sparse product (mixed-precision inner solves) */
 #define PP_K_BLOCK_APPLY32 9   /* FP32 block-Jacobi application */
 #define PP_K_KRYLOV32 10       /* FP32 Krylov reductions */
-#define PP_K_COUNT 11
+#define PP_K_STAGE_OP 11       /* FP64 stage operator with the preconditioner folded in, x + B x */
+#define PP_K_FOLD 12           /* products B = -c J_off D^-1 forming that operator (FP64 or FP32) */
+#define PP_K_STAGE_OP32 13     /* FP32 folded stage operator of the mixed-precision inner solves */
+#define PP_K_COUNT 14
 
 /* Starts timing every launch of kernel class `kind` (one class at a time; PP_K_NONE
    stops).  Resets the accumulated totals.  Not thread-safe: one host thread drives libpp. */

@@ -32,7 +32,7 @@ EXPORTED = [
     "pp_adam_f32", "pp_syevj_f64",
 ]
 PP_K = dict(none=0, jacobian=1, residual=2, stage_matvec=3, block_apply=4, block_inverse=5, krylov=6, other=7,
-            stage_matvec32=8, block_apply32=9, krylov32=10)
+            stage_matvec32=8, block_apply32=9, krylov32=10, stage_op=11, fold=12, stage_op32=13)
 
 
 class pp_config(C.Structure):
@@ -283,7 +283,7 @@ def pp_prof_read():
 
 
 def pp_prof_counts():
-    a = (C.c_int64 * 11)()
+    a = (C.c_int64 * 14)()
     _check(None, _lib.pp_prof_counts(a))
     return {k: a[v] for k, v in PP_K.items() if k != "none"}
 

@@ -99,6 +99,10 @@ struct pp_ctx {
   double* st_u = nullptr;       // [stages][nu] stage states
   double* st_JT = nullptr;      // [stages][ne*4*nb*nb] transposed block-columns (optional)
   double* st_AinvT = nullptr;   // [stages][ne*nb*nb] transposed inverses (optional; FP64 mode)
+  double* st_BN = nullptr;      // [stages][ne*3*nb*nb] folded operator blocks -c J_off D^-1 (optional; FP64 mode)
+  double* st_BT = nullptr;      // [stages][ne*3*nb*nb] folded transposed blocks (optional; FP64 mode)
+  float* st_BN32 = nullptr;     // mixed mode: FP32 folded blocks from the FP32 copies (optional)
+  float* st_BT32 = nullptr;
   float* st_J32 = nullptr;      // mixed mode: FP32 copies of J, J^T-columns and the inverses
   float* st_JT32 = nullptr;
   float* st_A32 = nullptr;

@@ -161,10 +161,12 @@ __global__ void __launch_bounds__(RES_WARPS * 32)
 // ------------------------------------------------------------------------ Jacobian
 // Shared-memory carve-up of k_jacobian (doubles), sized from the runtime degree.
 struct JacSmem {
-  int su, Cv, Cf, Tv, Tf, Tn, Wv, Wf, Wn, total;
+  int su, SV, SF, Cv, Cf, Tv, Tf, Tn, Wv, Wf, Wn, total;
   __host__ __device__ JacSmem(int nb, int Np, int nqv) {
     su = 0;
-    Cv = su + 4 * nb;
+    SV = su + 4 * nb;                 // [q][12]: U, grad U at the volume points
+    SF = SV + nqv * 12;               // [side][f][q][12]: both traces at the face points
+    Cv = SF + 2 * 3 * kMaxQf * 12;
     Cf = Cv + nqv * 4 * 2 * NSV;
     Tv = Cf + 3 * kMaxQf * 4 * NSF;
     Tf = Tv + nqv * 3 * Np;
@@ -221,75 +223,161 @@ __global__ void __launch_bounds__(JAC_THREADS)
   }
   frd.hd = Dual(fr.hd);
 
-  // phase 1a: volume seeds
-  for (int task = tid; task < nqv * NSV; task += JAC_THREADS) {
-    int q = task / NSV, s = task - q * NSV;
+  double* SV = smem + L.SV;
+  double* SF = smem + L.SF;
+  // phase 0: U and grad U at every quadrature point, once (both traces on faces)
+  for (int task = tid; task < nqv + 6 * nqf; task += JAC_THREADS) {
     double U0[4], dU0[4][2];
-    interp(su, Np, tb.phi_v + q * Np, tb.dphi_v + 2 * q * Np, P, U0, dU0);
-    Dual U[4], dU[4][2], vG[2], F[4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      U[a] = Dual(U0[a], s == a ? 1.0 : 0.0);
-      dU[a][0] = Dual(dU0[a][0], s == 4 + 2 * a ? 1.0 : 0.0);
-      dU[a][1] = Dual(dU0[a][1], s == 5 + 2 * a ? 1.0 : 0.0);
+    double* dst;
+    if (task < nqv) {
+      interp(su, Np, tb.phi_v + task * Np, tb.dphi_v + 2 * task * Np, P, U0, dU0);
+      dst = SV + task * 12;
+    } else {
+      const int t2 = task - nqv, side = t2 / (3 * nqf), r2 = t2 - side * 3 * nqf, f = r2 / nqf, q = r2 - f * nqf;
+      dst = SF + ((side * 3 + f) * kMaxQf + q) * 12;
+      if (side == 0 || m.tag[3 * e + f] != 0) {
+        interp(su, Np, tb.phi_f + (f * nqf + q) * Np, tb.dphi_f + 2 * (f * nqf + q) * Np, P, U0, dU0);
+      } else {
+        const int e2 = m.nbr[3 * e + f], g = m.nbrface[3 * e + f], qq = nqf - 1 - q;
+        double P2[4];
+        frame_P(fr, m.BinvT + 4 * e2, P2);
+        interp(su + (1 + f) * nb, Np, tb.phi_f + (g * nqf + qq) * Np, tb.dphi_f + 2 * (g * nqf + qq) * Np, P2, U0,
+               dU0);
+      }
     }
-    double X, Y;
-    ref_to_X(m, e, tb.xi_v[2 * q], tb.xi_v[2 * q + 1], X, Y);
-    mesh_velocity(frd, ph, X, Y, vG);
-    volume_flux(U, dU, vG, ph, F);
-    double wq = tb.w_v[q] * detB;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      Cv[((q * 4 + a) * 2 + 0) * NSV + s] = wq * (P[0] * F[a][0].d + P[2] * F[a][1].d);
-      Cv[((q * 4 + a) * 2 + 1) * NSV + s] = wq * (P[1] * F[a][0].d + P[3] * F[a][1].d);
+      dst[a] = U0[a];
+      dst[4 + 2 * a] = dU0[a][0];
+      dst[5 + 2 * a] = dU0[a][1];
     }
   }
-  // phase 1b: face seeds
+  __syncthreads();
+
+  // phase 1a: volume seeds.  The state seeds (4 per point) run the flux in dual numbers;
+  // the viscous flux is linear in grad U at fixed U, so the derivative for gradient seed
+  // (b, d) is the viscous flux of the unit gradient (8 per point, plain FP64).
+  for (int task = tid; task < nqv * NSV; task += JAC_THREADS) {
+    const bool dual = task < 4 * nqv;
+    const int q = dual ? task >> 2 : (task - 4 * nqv) >> 3;
+    const int s = dual ? (task & 3) : 4 + ((task - 4 * nqv) & 7);
+    const double* Sq = SV + q * 12;
+    double Fd[4][2];
+    if (dual) {
+      Dual U[4], dU[4][2], vG[2], F[4][2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        U[a] = Dual(Sq[a], s == a ? 1.0 : 0.0);
+        dU[a][0] = Dual(Sq[4 + 2 * a]);
+        dU[a][1] = Dual(Sq[5 + 2 * a]);
+      }
+      double X, Y;
+      ref_to_X(m, e, tb.xi_v[2 * q], tb.xi_v[2 * q + 1], X, Y);
+      mesh_velocity(frd, ph, X, Y, vG);
+      volume_flux(U, dU, vG, ph, F);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        Fd[a][0] = F[a][0].d;
+        Fd[a][1] = F[a][1].d;
+      }
+    } else {
+      double U[4], E[4][2], Fv[4][2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        U[a] = Sq[a];
+        E[a][0] = (s == 4 + 2 * a) ? 1.0 : 0.0;
+        E[a][1] = (s == 5 + 2 * a) ? 1.0 : 0.0;
+      }
+      viscous_flux(U, E, ph, false, Fv);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        Fd[a][0] = -Fv[a][0];
+        Fd[a][1] = -Fv[a][1];
+      }
+    }
+    const double wq = tb.w_v[q] * detB;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Cv[((q * 4 + a) * 2 + 0) * NSV + s] = wq * (P[0] * Fd[a][0] + P[2] * Fd[a][1]);
+      Cv[((q * 4 + a) * 2 + 1) * NSV + s] = wq * (P[1] * Fd[a][0] + P[3] * Fd[a][1]);
+    }
+  }
+  // phase 1b: face seeds (state seeds of both traces in dual numbers, gradient seeds by
+  // linearity of the viscous part: interior {F_vis} n halves, wall and far field full)
   for (int task = tid; task < 3 * nqf * NSF; task += JAC_THREADS) {
-    int f = task / (nqf * NSF);
-    int rem = task - f * nqf * NSF;
-    int q = rem / NSF, s = rem - q * NSF;
-    int tag = m.tag[3 * e + f];
+    const bool dual = task < 3 * nqf * 8;
+    int f, q, s;
+    if (dual) {
+      f = task / (nqf * 8);
+      const int rem = task - f * nqf * 8;
+      q = rem >> 3;
+      const int j = rem & 7;
+      s = j < 4 ? j : 8 + j;  // 0..3 (U-), 12..15 (U+)
+    } else {
+      const int t2 = task - 3 * nqf * 8;
+      f = t2 / (nqf * 16);
+      const int rem = t2 - f * nqf * 16;
+      q = rem >> 4;
+      const int j = rem & 15;
+      s = j < 8 ? 4 + j : 8 + j;  // 4..11 (grad U-), 16..23 (grad U+)
+    }
+    const int tag = m.tag[3 * e + f];
     double* out = Cf + ((f * kMaxQf + q) * 4) * NSF + s;
     if (tag != 0 && s >= 12) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) out[a * NSF] = 0.0;
       continue;
     }
-    double Um0[4], dUm0[4][2], Up0[4], dUp0[4][2];
-    interp(su, Np, tb.phi_f + (f * nqf + q) * Np, tb.dphi_f + 2 * (f * nqf + q) * Np, P, Um0, dUm0);
-    if (tag == 0) {
-      int e2 = m.nbr[3 * e + f], g = m.nbrface[3 * e + f], qq = nqf - 1 - q;
-      double P2[4];
-      frame_P(fr, m.BinvT + 4 * e2, P2);
-      interp(su + (1 + f) * nb, Np, tb.phi_f + (g * nqf + qq) * Np, tb.dphi_f + 2 * (g * nqf + qq) * Np, P2, Up0,
-             dUp0);
-    } else {
+    const double* Sm = SF + ((0 * 3 + f) * kMaxQf + q) * 12;
+    const double* Sp = SF + ((1 * 3 + f) * kMaxQf + q) * 12;
+    const double wl = tb.w_f[q] * m.L[3 * e + f];
+    if (dual) {
+      Dual Um[4], dUm[4][2], Up[4], dUp[4][2], n[2], vG[2], H[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        Up0[a] = Um0[a];
-        dUp0[a][0] = dUm0[a][0];
-        dUp0[a][1] = dUm0[a][1];
+        Um[a] = Dual(Sm[a], s == a ? 1.0 : 0.0);
+        dUm[a][0] = Dual(Sm[4 + 2 * a]);
+        dUm[a][1] = Dual(Sm[5 + 2 * a]);
+        Up[a] = Dual(Sp[a], s == 12 + a ? 1.0 : 0.0);
+        dUp[a][0] = Dual(Sp[4 + 2 * a]);
+        dUp[a][1] = Dual(Sp[5 + 2 * a]);
       }
-    }
-    Dual Um[4], dUm[4][2], Up[4], dUp[4][2], n[2], vG[2], H[4];
+      rotate_normal(frd, m.N + 6 * e + 2 * f, n);
+      double X, Y;
+      ref_to_X(m, e, tb.xi_f[2 * (f * nqf + q)], tb.xi_f[2 * (f * nqf + q) + 1], X, Y);
+      mesh_velocity(frd, ph, X, Y, vG);
+      face_flux(tag, Um, dUm, Up, dUp, n, vG, m.sigma[3 * e + f], ph, H);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      Um[a] = Dual(Um0[a], s == a ? 1.0 : 0.0);
-      dUm[a][0] = Dual(dUm0[a][0], s == 4 + 2 * a ? 1.0 : 0.0);
-      dUm[a][1] = Dual(dUm0[a][1], s == 5 + 2 * a ? 1.0 : 0.0);
-      Up[a] = Dual(Up0[a], s == 12 + a ? 1.0 : 0.0);
-      dUp[a][0] = Dual(dUp0[a][0], s == 16 + 2 * a ? 1.0 : 0.0);
-      dUp[a][1] = Dual(dUp0[a][1], s == 17 + 2 * a ? 1.0 : 0.0);
-    }
-    rotate_normal(frd, m.N + 6 * e + 2 * f, n);
-    double X, Y;
-    ref_to_X(m, e, tb.xi_f[2 * (f * nqf + q)], tb.xi_f[2 * (f * nqf + q) + 1], X, Y);
-    mesh_velocity(frd, ph, X, Y, vG);
-    face_flux(tag, Um, dUm, Up, dUp, n, vG, m.sigma[3 * e + f], ph, H);
-    double wl = tb.w_f[q] * m.L[3 * e + f];
+      for (int a = 0; a < 4; ++a) out[a * NSF] = wl * H[a].d;
+    } else {
+      const bool plus = s >= 16;
+      const int b = ((plus ? s - 16 : s - 4) >> 1), d = (plus ? s - 16 : s - 4) & 1;
+      const double* Ss = plus ? Sp : Sm;
+      double U[4], E[4][2], Fv[4][2], n[2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) out[a * NSF] = wl * H[a].d;
+      for (int a = 0; a < 4; ++a) {
+        U[a] = Ss[a];
+        E[a][0] = (a == b && d == 0) ? 1.0 : 0.0;
+        E[a][1] = (a == b && d == 1) ? 1.0 : 0.0;
+      }
+      rotate_normal(fr, m.N + 6 * e + 2 * f, n);
+      double scale = tag == 0 ? -0.5 : -1.0;
+      if (tag == 1) {
+        // wall: the viscous flux is evaluated at the ghost state (interior density and
+        // internal energy, wall velocity) with the interior gradient, adiabatic
+        double X, Y, vG[2];
+        ref_to_X(m, e, tb.xi_f[2 * (f * nqf + q)], tb.xi_f[2 * (f * nqf + q) + 1], X, Y);
+        mesh_velocity(fr, ph, X, Y, vG);
+        const double r = U[0];
+        const double eint = U[3] / r - 0.5 * (U[1] * U[1] + U[2] * U[2]) / (r * r);
+        double Ub[4] = {r, r * vG[0], r * vG[1], r * (eint + 0.5 * (vG[0] * vG[0] + vG[1] * vG[1]))};
+        viscous_flux(Ub, E, ph, true, Fv);
+      } else {
+        viscous_flux(U, E, ph, false, Fv);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) out[a * NSF] = wl * scale * (Fv[a][0] * n[0] + Fv[a][1] * n[1]);
+    }
   }
   // trial tables: basis values and physical gradients at the volume / face points
   for (int idx = tid; idx < nqv * Np; idx += JAC_THREADS) {

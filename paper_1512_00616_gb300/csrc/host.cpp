@@ -305,11 +305,11 @@ int ensure_store(pp_ctx* ctx, const pp_mesh* mesh, int Nt) {
   }
   if (ctx->store_stages >= stages && ctx->lin_mesh == mesh) return PP_OK;
   auto release = [&]() {
-    for (double** p : {&ctx->st_J, &ctx->st_Ainv, &ctx->st_u, &ctx->st_JT, &ctx->st_AinvT}) {
+    for (double** p : {&ctx->st_J, &ctx->st_Ainv, &ctx->st_u, &ctx->st_JT, &ctx->st_AinvT, &ctx->st_BN, &ctx->st_BT}) {
       cudaFree(*p);
       *p = nullptr;
     }
-    for (float** p : {&ctx->st_J32, &ctx->st_JT32, &ctx->st_A32, &ctx->st_AT32}) {
+    for (float** p : {&ctx->st_J32, &ctx->st_JT32, &ctx->st_A32, &ctx->st_AT32, &ctx->st_BN32, &ctx->st_BT32}) {
       cudaFree(*p);
       *p = nullptr;
     }
@@ -332,9 +332,35 @@ int ensure_store(pp_ctx* ctx, const pp_mesh* mesh, int Nt) {
     release();
     return set_error(ctx, PP_ENOMEM, "linearization store does not fit in device memory");
   }
+  size_t fr = 0, tot = 0;
+  // the block-Jacobi preconditioner folded into the stage operator (three neighbour blocks
+  // per element, normal and transposed; FP64, or FP32 for the inner solves of the mixed
+  // path), kept while 8 GB of device memory stay free
+  {
+    const size_t nB = stages * mesh->ne * 3 * nb2;
+    const size_t word = mixed ? sizeof(float) : sizeof(double);
+    cudaMemGetInfo(&fr, &tot);
+    if (fr > word * 2 * nB + ((size_t)8 << 30)) {
+      bool okB;
+      if (!mixed)
+        okB = cudaMalloc(&ctx->st_BN, sizeof(double) * nB) == cudaSuccess &&
+              cudaMalloc(&ctx->st_BT, sizeof(double) * nB) == cudaSuccess;
+      else
+        okB = cudaMalloc(&ctx->st_BN32, sizeof(float) * nB) == cudaSuccess &&
+              cudaMalloc(&ctx->st_BT32, sizeof(float) * nB) == cudaSuccess;
+      if (!okB) {
+        cudaGetLastError();
+        cudaFree(ctx->st_BN);
+        cudaFree(ctx->st_BT);
+        cudaFree(ctx->st_BN32);
+        cudaFree(ctx->st_BT32);
+        ctx->st_BN = ctx->st_BT = nullptr;
+        ctx->st_BN32 = ctx->st_BT32 = nullptr;
+      }
+    }
+  }
   // FP64 transposed copies let the adjoint stream row-major blocks with the normal
   // kernels; they are kept only while at least 8 GB of device memory stay free
-  size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   const size_t extra = sizeof(double) * (nJ + (mixed ? 0 : nA));
   if (fr > extra + ((size_t)8 << 30)) {
@@ -496,10 +522,14 @@ int pp_destroy(pp_ctx* ctx) {
   cudaFree(ctx->st_u);
   cudaFree(ctx->st_JT);
   cudaFree(ctx->st_AinvT);
+  cudaFree(ctx->st_BN);
+  cudaFree(ctx->st_BT);
   cudaFree(ctx->st_J32);
   cudaFree(ctx->st_JT32);
   cudaFree(ctx->st_A32);
   cudaFree(ctx->st_AT32);
+  cudaFree(ctx->st_BN32);
+  cudaFree(ctx->st_BT32);
   cudaFree(ctx->ck_u);
   cudaFree(ctx->ck_k);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

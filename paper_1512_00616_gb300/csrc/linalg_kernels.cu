@@ -13,9 +13,10 @@
 //    element Jacobian (diagonal + 3 face-neighbour blocks).
 //  - k_transpose_blocks: per element, the transposed blocks of its block-column, so
 //    that J^T x runs through the same row-streaming kernel as J x.
-//  - k_krylov<S>: fused classical Gram-Schmidt (twice) steps with a deterministic
-//    two-level reduction (per-block partials, summed in a fixed order by the block that
-//    finishes last), and the GMRES Givens update fused into the norm kernel.
+//  - k_cgs<KB, S>: fused classical Gram-Schmidt passes of the Arnoldi step (a second pass
+//    only when the first cancels more than half of |w|^2), with a deterministic
+//    reduction (warp, CTA, then the CTA that finishes last in a fixed order), and the
+//    GMRES Givens update fused into the norm pass.
 //
 // GB300 note: its FP64 pipe issues ~2 DFMA per clock per SM, so FP64 block products are
 // ALU-bound (~21 us for the 4 x 40 x 40 x 2048 Jacobian product) before they are
@@ -362,6 +363,65 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Preconditioner folded into the stage operator (one CTA per element face, both nb x nb
+// operands staged in shared memory, column-major in and out):
+//   BN[e][f] = -c J[e][1+f] Ainv[e2]                    e2 = nbr(e, f)
+//   BT[e][f] = (-c Ainv[e2] J[e2][1+g])^T              g = nbrface(e, f)
+// so that (M - cJ) D^{-1} = I + BN and (M - cJ)^T D^{-T} = I + BT, with D = M - c J_ee the
+// block diagonal (Ainv its inverse) and BN, BT zero on boundary faces.
+template <int NB, class S>
+__global__ void __launch_bounds__(256)
+    k_fold_blocks(DevMesh m, const S* __restrict__ J, const S* __restrict__ Ainv, double c, S* __restrict__ BN,
+                  S* __restrict__ BT) {
+  extern __shared__ __align__(16) unsigned char fsm_raw[];
+  S* P = reinterpret_cast<S*>(fsm_raw);
+  S* Q = P + NB * NB;
+  constexpr int nb2 = NB * NB;
+  const int e = blockIdx.x / 3, f = blockIdx.x - 3 * (blockIdx.x / 3);
+  const int e2 = m.nbr[3 * e + f];
+  S* outN = BN ? BN + ((size_t)e * 3 + f) * nb2 : nullptr;
+  S* outT = BT ? BT + ((size_t)e * 3 + f) * nb2 : nullptr;
+  if (e2 < 0) {
+    for (int i = threadIdx.x; i < nb2; i += blockDim.x) {
+      if (outN) outN[i] = S(0);
+      if (outT) outT[i] = S(0);
+    }
+    return;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    S* out = pass == 0 ? outN : outT;
+    if (!out) continue;
+    const S* Pg = pass == 0 ? J + ((size_t)e * 4 + 1 + f) * nb2 : Ainv + (size_t)e2 * nb2;
+    const S* Qg = pass == 0 ? Ainv + (size_t)e2 * nb2 : J + ((size_t)e2 * 4 + 1 + m.nbrface[3 * e + f]) * nb2;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb2; i += blockDim.x) {
+      P[i] = Pg[i];
+      Q[i] = Qg[i];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb2; idx += blockDim.x) {
+      const int cc = idx / NB, r = idx - cc * NB;  // output (r, cc), column-major
+      S a0 = S(0), a1 = S(0);
+      if (pass == 0) {
+        // (P Q)(r, cc) = sum_k P(r, k) Q(k, cc)
+#pragma unroll 8
+        for (int k = 0; k < NB; k += 2) {
+          a0 += P[k * NB + r] * Q[cc * NB + k];
+          a1 += P[(k + 1) * NB + r] * Q[cc * NB + k + 1];
+        }
+      } else {
+        // ((P Q)^T)(r, cc) = (P Q)(cc, r) = sum_k P(cc, k) Q(k, r)
+#pragma unroll 8
+        for (int k = 0; k < NB; k += 2) {
+          a0 += P[k * NB + cc] * Q[r * NB + k];
+          a1 += P[(k + 1) * NB + cc] * Q[r * NB + k + 1];
+        }
+      }
+      out[idx] = S(-c) * (a0 + a1);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ vector kernels
 template <class S>
 __global__ void k_lincomb(int64_t n, S* y, int nterms, double c0, double c1, double c2, double c3, const S* x0,
@@ -431,36 +491,6 @@ __device__ __forceinline__ bool finish(int k, double* partial, unsigned* counter
   return true;
 }
 
-// dot products of w with vectors V_{j0..j0+kb-1} accumulated over this thread's indices
-template <int KB, class S>
-__device__ __forceinline__ void dots_batch(int64_t n, const S* __restrict__ V, int64_t ldv, int j0, int kb,
-                                           const S* w, double* partial, int ld) {
-  S acc[KB];
-#pragma unroll
-  for (int t = 0; t < KB; ++t) acc[t] = S(0);
-  const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += stride) {
-    const S wi = w[i];
-#pragma unroll
-    for (int t = 0; t < KB; ++t)
-      if (t < kb) acc[t] += V[(int64_t)(j0 + t) * ldv + i] * wi;
-  }
-  block_partials<KB, S>(acc, kb, partial, ld, j0);
-}
-
-template <class S>
-__device__ __forceinline__ void dots_any(int64_t n, const S* V, int64_t ldv, int k, const S* w, double* partial) {
-  for (int j0 = 0; j0 < k; j0 += 32) {
-    const int kb = min(32, k - j0);
-    if (kb > 16) dots_batch<32, S>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 8) dots_batch<16, S>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 4) dots_batch<8, S>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 2) dots_batch<4, S>(n, V, ldv, j0, kb, w, partial, k);
-    else if (kb > 1) dots_batch<2, S>(n, V, ldv, j0, kb, w, partial, k);
-    else dots_batch<1, S>(n, V, ldv, j0, kb, w, partial, k);
-  }
-}
-
 struct GivensArgs {
   int j, m;
   const double* h1;
@@ -519,34 +549,216 @@ __device__ __forceinline__ void givens_update(const GivensArgs& a, double nrm2) 
   for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = col[i];
 }
 
-// mode 0: out = V^T w;  mode 1: w -= V h, out = V^T w;  mode 2: w -= V h, out[0] = w.w
-// (then the Givens update if gv.H != null);  mode 3: out[0] = V_0 . w
+// ------------------------------------------------------------------ Gram-Schmidt kernels
+// One kernel per classical Gram-Schmidt pass of the Arnoldi step:
+//   mode 0: out = V^T w (and out[k] = w.w when self is set)
+//   mode 1: w -= V h, then out = V^T w
+//   mode 2: w -= V h, then out[0] = w.w (and the Givens update when gv.H is set)
+//   mode 3: out[0] = V_0 . w
+// GB300 issues about 1.7 FP64 FMAs per clock per SM, so every FP64 instruction counts:
+// at most one CTA per SM, each thread accumulates several vector entries before the
+// single warp reduce-scatter, and the unrolled loops run over KB = k rounded up to a
+// multiple of 4.  For k <= KB (up to 40) the k basis entries of an index are loaded once
+// (all in flight together) and serve both the update and the dots.  Reduction, in a
+// fixed order at every level so that results are bitwise reproducible: warp
+// reduce-scatter -> CTA partials -> the CTA that finishes last sums the CTA partials.
+constexpr int CGS_T = 256;
+constexpr int CGS_MAX_BLOCKS = 152;
+constexpr int CGS_MAXK = 64;
+constexpr int CGS_MAXKB = 40;
+
+template <int KB>
+struct Pow2Up {
+  static constexpr int value =
+      KB <= 1 ? 1 : KB <= 2 ? 2 : KB <= 4 ? 4 : KB <= 8 ? 8 : KB <= 16 ? 16 : KB <= 32 ? 32 : 64;
+};
+
+// v[KB] per thread -> bp[j0 + t] (shared), t < kb; all CTA threads call it.  KB <= 64:
+// a 64-wide reduction runs as two 32-wide halves.
+template <int KB, class S>
+__device__ __forceinline__ void cta_reduce(S* v, int kb, double* bp, int j0) {
+  if constexpr (KB > 32) {
+    cta_reduce<32, S>(v, kb < 32 ? kb : 32, bp, j0);
+    if (kb > 32) cta_reduce<32, S>(v + 32, kb - 32, bp, j0 + 32);
+  } else {
+    __shared__ double red[32][CGS_T / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_reduce_scatter<KB, S>(v, lane);
+    constexpr int sh = 5 - ILog2<KB>::value;
+    if ((lane & ((1 << sh) - 1)) == 0) red[lane >> sh][warp] = (double)v[0];
+    __syncthreads();
+    if (threadIdx.x < kb) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < CGS_T / 32; ++w) s += red[threadIdx.x][w];
+      bp[j0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Grid level of the reduction of the CTA partials bp[0..nk).  Returns true in the one
+// CTA that holds the final sums in out[] (the last CTA to arrive).
+__device__ __forceinline__ bool cgs_finish(int nk, const double* bp, double* partial, unsigned* counter,
+                                           double* out) {
+  for (int t = threadIdx.x; t < nk; t += CGS_T) partial[(size_t)blockIdx.x * nk + t] = bp[t];
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1u);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = gridDim.x;
+  for (int j = warp; j < nk; j += CGS_T / 32) {
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nb; b += 64) {
+      s0 += __ldcg(partial + (size_t)b * nk + j);
+      s1 += __ldcg(partial + (size_t)(b + 32) * nk + j);
+    }
+    if (b < nb) s0 += __ldcg(partial + (size_t)b * nk + j);
+    double s = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[j] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
+}
+
 template <class S>
-__global__ void __launch_bounds__(RED_THREADS)
-    k_krylov(int mode, int64_t n, const S* __restrict__ V, int64_t ldv, int k, const double* __restrict__ h,
-             S* __restrict__ w, double* __restrict__ out, double* __restrict__ partial, unsigned* counter,
-             GivensArgs gv) {
-  const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-  const int64_t i0 = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x;
-  if (mode == 1 || mode == 2) {
-    for (int64_t i = i0; i < n; i += stride) {
-      S s = w[i];
-      for (int j = 0; j < k; ++j) s -= S(h[j]) * V[j * ldv + i];
-      w[i] = s;
+struct CgsArgs {
+  int mode;           // 0 dots, 1 update + dots, 2 update + norm, 3 single dot
+  int self;           // mode 0: also out[k] = w.w
+  int64_t n;
+  const S* V;
+  int64_t ldv;
+  int k;
+  const double* h;    // update coefficients (modes 1, 2)
+  const double* chk;  // non-null: selective reorthogonalization on chk[0..k), chk[k] = |w|^2 before
+  S* w;
+  double* out;
+  double* out_nrm;    // mode 1 without reorthogonalization: |w|^2 goes here, out[0..k) = 0
+  double* partial;
+  unsigned* counter;
+  GivensArgs gv;
+};
+
+template <int KB, class S>
+__global__ void __launch_bounds__(CGS_T, 1) k_cgs(CgsArgs<S> a) {
+  constexpr int K2 = Pow2Up<KB>::value;
+  __shared__ double hs[CGS_MAXK + 1];
+  __shared__ double bp[CGS_MAXK + 1];
+  __shared__ int s_need;
+  const int k = a.k;
+  const int64_t n = a.n;
+  const S* __restrict__ V = a.V;
+  S* __restrict__ w = a.w;
+  const int64_t ldv = a.ldv;
+  int mode = a.mode;
+  bool to_norm = false;
+  if (a.chk) {
+    // second pass needed?  |w - V h1|^2 = |w|^2 - |h1|^2 in exact arithmetic; the pass is
+    // repeated when more than half of |w|^2 cancelled (|w - V h1| < |w| / sqrt 2).  Every
+    // CTA takes the same decision from the same first-pass coefficients.
+    if (threadIdx.x < 32) {
+      double hh = 0.0;
+      for (int t = threadIdx.x; t < k; t += 32) hh += a.chk[t] * a.chk[t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+      if (threadIdx.x == 0) s_need = (hh <= 0.5 * a.chk[k]) ? 0 : 1;
+    }
+    __syncthreads();
+    const bool need = s_need != 0;
+    if (mode == 2 && !need) return;  // the second pass was not needed: nothing left to do
+    if (mode == 1 && !need) {        // update with h1, then the norm instead of a second pass
+      mode = 2;
+      to_norm = true;
     }
   }
-  if (mode == 2) {
-    dots_batch<1, S>(n, w, 0, 0, 1, w, partial, 1);
-    if (finish(1, partial, counter, out) && gv.H) givens_update(gv, out[0]);
-    return;
+  const bool upd = (mode == 1 || mode == 2);
+  for (int t = threadIdx.x; t < CGS_MAXK; t += CGS_T) hs[t] = (upd && t < k) ? a.h[t] : 0.0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * CGS_T;
+  const int64_t i0 = (int64_t)blockIdx.x * CGS_T + threadIdx.x;
+  const bool self = (mode == 0 && a.self);
+  const int nk = (mode == 0 || mode == 1) ? k : 1;
+  S accs[1] = {S(0)};
+  if (k <= KB) {
+    S acc[K2];
+#pragma unroll
+    for (int t = 0; t < K2; ++t) acc[t] = S(0);
+    for (int64_t i = i0; i < n; i += stride) {
+      S v[KB];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
+      S s = w[i];
+      if (upd) {
+#pragma unroll
+        for (int t = 0; t < KB; ++t) s -= S(hs[t]) * v[t];
+        w[i] = s;
+      }
+      if (mode == 2) {
+        acc[0] += s * s;
+      } else if (mode == 3) {
+        acc[0] += v[0] * s;
+      } else {
+#pragma unroll
+        for (int t = 0; t < KB; ++t) acc[t] += v[t] * s;
+        if (self) accs[0] += s * s;
+      }
+    }
+    if (nk == 1) cta_reduce<1, S>(acc, 1, bp, 0);
+    else cta_reduce<K2, S>(acc, nk, bp, 0);
+  } else {
+    // k > KB: update in chunks of KB loads, then one dot pass per chunk (re-reads)
+    if (upd) {
+      for (int64_t i = i0; i < n; i += stride) {
+        S s = w[i];
+        for (int c0 = 0; c0 < k; c0 += KB) {
+          S v[KB];
+#pragma unroll
+          for (int t = 0; t < KB; ++t) v[t] = (c0 + t < k) ? V[(int64_t)(c0 + t) * ldv + i] : S(0);
+#pragma unroll
+          for (int t = 0; t < KB; ++t) s -= S(hs[c0 + t]) * v[t];
+        }
+        w[i] = s;
+      }
+    }
+    if (mode == 2) {
+      S acc[1] = {S(0)};
+      for (int64_t i = i0; i < n; i += stride) {
+        const S s = w[i];
+        acc[0] += s * s;
+      }
+      cta_reduce<1, S>(acc, 1, bp, 0);
+    } else {
+      for (int c0 = 0; c0 < k; c0 += KB) {
+        S acc[K2];
+#pragma unroll
+        for (int t = 0; t < K2; ++t) acc[t] = S(0);
+        for (int64_t i = i0; i < n; i += stride) {
+          const S s = w[i];
+#pragma unroll
+          for (int t = 0; t < KB; ++t)
+            if (c0 + t < k) acc[t] += V[(int64_t)(c0 + t) * ldv + i] * s;
+          if (self && c0 == 0) accs[0] += s * s;
+        }
+        cta_reduce<K2, S>(acc, min(KB, k - c0), bp, c0);
+      }
+    }
   }
-  if (mode == 3) {
-    dots_batch<1, S>(n, V, 0, 0, 1, w, partial, 1);
-    finish(1, partial, counter, out);
-    return;
+  if (self) cta_reduce<1, S>(accs, 1, bp, k);
+  double* out = to_norm ? a.out_nrm : a.out;
+  if (!cgs_finish(nk + (self ? 1 : 0), bp, a.partial, a.counter, out)) return;
+  if (to_norm) {
+    for (int t = threadIdx.x; t < k; t += CGS_T) a.out[t] = 0.0;  // no second-pass coefficients
+    __syncthreads();
   }
-  dots_any<S>(n, V, ldv, k, w, partial);
-  finish(k, partial, counter, out);
+  if (mode == 2 && a.gv.H) givens_update(a.gv, out[0]);
 }
 
 // out[j] = sum_e per_elem[e*k + j], k <= 8
@@ -578,14 +790,27 @@ __global__ void k_gmres_init(const double* bb, double rtol, double atol, int fir
   stat[7] = -1.0;
 }
 
-// y = -(H^{-1} g) on the leading ncols x ncols triangle (negated for the fused update kernel)
-__global__ void k_gmres_backsolve(int ncols, int m, const double* H, const double* g, double* y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// y = -(H^{-1} g) on the leading ncols x ncols triangle (negated for the fused update
+// kernel).  The triangle is staged in shared memory; column-oriented back substitution,
+// one column per step, the remaining right-hand side updated by the whole block in a
+// fixed order (each entry by one thread).
+__global__ void __launch_bounds__(256) k_gmres_backsolve(int ncols, int m, const double* H, const double* g,
+                                                         double* y) {
+  __shared__ double Hs[64 * 65];
+  __shared__ double rhs[64];
+  for (int idx = threadIdx.x; idx < ncols * ncols; idx += blockDim.x) {
+    const int c = idx / ncols, r = idx - c * ncols;
+    Hs[c * 65 + r] = H[(size_t)c * (m + 1) + r];
+  }
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) rhs[i] = g[i];
+  __syncthreads();
   for (int i = ncols - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int k = i + 1; k < ncols; ++k) s += H[(size_t)k * (m + 1) + i] * y[k];  // y holds negated values
-    const double d = H[(size_t)i * (m + 1) + i];
-    y[i] = d != 0.0 ? -s / d : 0.0;
+    const double d = Hs[i * 65 + i];
+    const double yi = d != 0.0 ? rhs[i] / d : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = -yi;
+    for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= Hs[i * 65 + r] * yi;
+    __syncthreads();
   }
 }
 
@@ -615,6 +840,8 @@ template <class S>
 cudaError_t launch_stage_matvec(const DevMesh& m, const DevTables& tb, const S* J, double alpha, double beta,
                                 const S* x, S* y, int trans, cudaStream_t st) {
   ProfScope ps(sizeof(S) == 8 ? PP_K_STAGE_MATVEC : PP_K_STAGE_MATVEC32, st);
+  if (!trans && beta != 0.0 && stream_rows_supported<S>(tb.nb, J, x, y))
+    return launch_stream_rows<S>(m, tb, tb.nb, 4, J, alpha, beta, x, y, st);
   const int g = m.ne, b = 128;
 #define PP_SMV(NBV)                                                                        \
   case NBV:                                                                                \
@@ -636,6 +863,10 @@ template <class S>
 cudaError_t launch_block_apply(const DevMesh& m, int nb, const S* Ainv, const S* x, S* y, int trans,
                                cudaStream_t st) {
   ProfScope ps(sizeof(S) == 8 ? PP_K_BLOCK_APPLY : PP_K_BLOCK_APPLY32, st);
+  if (!trans && stream_rows_supported<S>(nb, Ainv, x, y)) {
+    DevTables none{};
+    return launch_stream_rows<S>(m, none, nb, 1, Ainv, 0.0, 1.0, x, y, st);
+  }
   const int g = m.ne, b = 128;
 #define PP_BAP(NBV)                                                             \
   case NBV:                                                                     \
@@ -650,6 +881,35 @@ cudaError_t launch_block_apply(const DevMesh& m, int nb, const S* Ainv, const S*
     default: return cudaErrorInvalidValue;
   }
 #undef PP_BAP
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_fold_blocks(const DevMesh& m, int nb, const S* J, const S* Ainv, double c, S* BN, S* BT,
+                               cudaStream_t st) {
+  ProfScope ps(PP_K_FOLD, st);
+  const size_t smem = sizeof(S) * 2 * nb * nb;
+#define PP_FOLD(NBV)                                                                                     \
+  case NBV: {                                                                                            \
+    static bool attr = false;                                                                            \
+    if (!attr) {                                                                                         \
+      cudaError_t e = cudaFuncSetAttribute(k_fold_blocks<NBV, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                           (int)smem);                                                  \
+      if (e != cudaSuccess) return e;                                                                    \
+      attr = true;                                                                                       \
+    }                                                                                                    \
+    k_fold_blocks<NBV, S><<<m.ne * 3, 256, smem, st>>>(m, J, Ainv, c, BN, BT);                           \
+    break;                                                                                               \
+  }
+  switch (nb) {
+    PP_FOLD(12)
+    PP_FOLD(24)
+    PP_FOLD(40)
+    PP_FOLD(60)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef PP_FOLD
   return cudaGetLastError();
 }
 
@@ -692,33 +952,84 @@ cudaError_t launch_gmres_init(const double* bb, double rtol, double atol, int fi
 
 cudaError_t launch_gmres_backsolve(int ncols, int m, const double* H, const double* g, double* y, cudaStream_t st) {
   ProfScope ps(PP_K_OTHER, st);
-  k_gmres_backsolve<<<1, 32, 0, st>>>(ncols, m, H, g, y);
+  k_gmres_backsolve<<<1, 256, 0, st>>>(ncols, m, H, g, y);
   return cudaGetLastError();
+}
+
+// One CTA per SM at most (fewer for short vectors).
+int cgs_blocks(int64_t n) {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = CGS_MAX_BLOCKS;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cap = sms < CGS_MAX_BLOCKS ? sms : CGS_MAX_BLOCKS;
+    if (cap < 1) cap = 1;
+  }
+  int64_t b = (n + CGS_T - 1) / CGS_T;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <class S>
+cudaError_t launch_cgs(const CgsArgs<S>& a, cudaStream_t st) {
+  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
+  if (a.k < 1 || a.k > CGS_MAXK) return cudaErrorInvalidValue;
+  const int g = cgs_blocks(a.n);
+  switch ((a.k + 3) / 4) {
+#define PP_CGS(Q) \
+  case Q:         \
+    k_cgs<4 * Q, S><<<g, CGS_T, 0, st>>>(a); \
+    break;
+    PP_CGS(1)
+    PP_CGS(2)
+    PP_CGS(3)
+    PP_CGS(4)
+    PP_CGS(5)
+    PP_CGS(6)
+    PP_CGS(7)
+    PP_CGS(8)
+    PP_CGS(9)
+    PP_CGS(10)
+    default:
+      k_cgs<32, S><<<g, CGS_T, 0, st>>>(a);  // k > 40: chunked path
+#undef PP_CGS
+  }
+  return cudaGetLastError();
+}
+
+template <class S>
+CgsArgs<S> cgs_args(int mode, int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
+                    double* partial, unsigned* counter) {
+  CgsArgs<S> a{};
+  a.mode = mode;
+  a.n = n;
+  a.V = V;
+  a.ldv = ldv;
+  a.k = k;
+  a.h = h;
+  a.w = w;
+  a.out = out;
+  a.partial = partial;
+  a.counter = counter;
+  return a;
 }
 
 template <class S>
 cudaError_t launch_mdot(int64_t n, const S* V, int64_t ldv, int k, const S* w, double* out, double* partial,
                         unsigned* counter, cudaStream_t st) {
-  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
-  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(0, n, V, ldv, k, nullptr, const_cast<S*>(w), out, partial,
-                                                     counter, GivensArgs{});
-  return cudaGetLastError();
+  return launch_cgs<S>(cgs_args<S>(0, n, V, ldv, k, nullptr, const_cast<S*>(w), out, partial, counter), st);
 }
 
 template <class S>
 cudaError_t launch_update_mdot(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
                                double* partial, unsigned* counter, cudaStream_t st) {
-  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
-  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(1, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
-  return cudaGetLastError();
+  return launch_cgs<S>(cgs_args<S>(1, n, V, ldv, k, h, w, out, partial, counter), st);
 }
 
 template <class S>
 cudaError_t launch_update_norm2(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
                                 double* partial, unsigned* counter, cudaStream_t st) {
-  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
-  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, GivensArgs{});
-  return cudaGetLastError();
+  return launch_cgs<S>(cgs_args<S>(2, n, V, ldv, k, h, w, out, partial, counter), st);
 }
 
 template <class S>
@@ -726,19 +1037,38 @@ cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k
                                        double* partial, unsigned* counter, int j, int m, const double* h1,
                                        const double* h2, double* H, double* cs, double* sn, double* g, double* stat,
                                        cudaStream_t st) {
-  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
-  GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat};
-  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(2, n, V, ldv, k, h, w, out, partial, counter, gv);
-  return cudaGetLastError();
+  CgsArgs<S> a = cgs_args<S>(2, n, V, ldv, k, h, w, out, partial, counter);
+  a.gv = GivensArgs{j, m, h1, h2, H, cs, sn, g, stat};
+  return launch_cgs<S>(a, st);
+}
+
+template <class S>
+cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w, double* h1, double* h2,
+                                 double* nrm, double* partial, unsigned* counter, int j, int m, double* H, double* cs,
+                                 double* sn, double* g, double* stat, cudaStream_t st) {
+  const GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat};
+  // pass 1: h1 = V^T w and |w|^2
+  CgsArgs<S> a = cgs_args<S>(0, n, V, ldv, k, nullptr, w, h1, partial, counter);
+  a.self = 1;
+  cudaError_t e = launch_cgs<S>(a, st);
+  if (e != cudaSuccess) return e;
+  // pass 2: w -= V h1; then h2 = V^T w if reorthogonalization is needed, else |w|^2 + Givens
+  a = cgs_args<S>(1, n, V, ldv, k, h1, w, h2, partial, counter);
+  a.chk = h1;
+  a.out_nrm = nrm;
+  a.gv = gv;
+  if ((e = launch_cgs<S>(a, st)) != cudaSuccess) return e;
+  // pass 3 (only if needed): w -= V h2, |w|^2 + Givens
+  a = cgs_args<S>(2, n, V, ldv, k, h2, w, nrm, partial, counter);
+  a.chk = h1;
+  a.gv = gv;
+  return launch_cgs<S>(a, st);
 }
 
 template <class S>
 cudaError_t launch_dot(int64_t n, const S* x, const S* y, double* out, double* partial, unsigned* counter,
                        cudaStream_t st) {
-  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
-  k_krylov<S><<<red_blocks(n), RED_THREADS, 0, st>>>(3, n, x, 0, 1, nullptr, const_cast<S*>(y), out, partial,
-                                                     counter, GivensArgs{});
-  return cudaGetLastError();
+  return launch_cgs<S>(cgs_args<S>(3, n, x, 0, 1, nullptr, const_cast<S*>(y), out, partial, counter), st);
 }
 
 cudaError_t launch_colsum(int ne, int k, const double* per_elem, double* out, double* partial, unsigned* counter,
@@ -769,6 +1099,11 @@ cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaSt
                                              unsigned*, cudaStream_t);                                              \
   template cudaError_t launch_update_norm2<S>(int64_t, const S*, int64_t, int, const double*, S*, double*, double*, \
                                               unsigned*, cudaStream_t);                                             \
+  template cudaError_t launch_fold_blocks<S>(const DevMesh&, int, const S*, const S*, double, S*, S*,         \
+                                             cudaStream_t);                                                     \
+  template cudaError_t launch_arnoldi_ortho<S>(int64_t, const S*, int64_t, int, S*, double*, double*, double*,  \
+                                                 double*, unsigned*, int, int, double*, double*, double*, double*,  \
+                                                 double*, cudaStream_t);                                            \
   template cudaError_t launch_update_norm2_givens<S>(int64_t, const S*, int64_t, int, const double*, S*, double*,   \
                                                      double*, unsigned*, int, int, const double*, const double*,    \
                                                      double*, double*, double*, double*, double*, cudaStream_t);    \

@@ -171,6 +171,14 @@ template <class S>
 cudaError_t launch_update_norm2(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
                                 double* partial, unsigned* counter, cudaStream_t st);
 // w -= V h[0:k]; out[0] = w . w; then the GMRES Givens update of Hessenberg column j
+// One Arnoldi orthogonalization step against V[0..k) with selective reorthogonalization
+// (classical Gram-Schmidt, a second pass only when more than half of |w|^2 cancels),
+// ending with the Givens update of Hessenberg column j: h1[0..k] <- (V^T w, |w|^2),
+// h2 the second-pass coefficients (zero when skipped), nrm[0] = |w|^2 after.
+template <class S>
+cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w, double* h1, double* h2,
+                                 double* nrm, double* partial, unsigned* counter, int j, int m, double* H, double* cs,
+                                 double* sn, double* g, double* stat, cudaStream_t st);
 template <class S>
 cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
                                        double* partial, unsigned* counter, int j, int m, const double* h1,
@@ -184,6 +192,19 @@ cudaError_t launch_dot(int64_t n, const S* x, const S* y, double* out, double* p
 cudaError_t launch_colsum(int ne, int k, const double* per_elem, double* out, double* partial, unsigned* counter,
                           cudaStream_t st);
 
+// TMA-staged block-row products (stream_kernels.cu): nblk = 4, the stage operator
+// y = alpha M x + beta J x; nblk = 1, the block product y = A x.  Normal products only.
+template <class S>
+bool stream_rows_supported(int nb, const S* B, const S* x, const S* y);
+template <class S>
+cudaError_t launch_stream_rows(const DevMesh& m, const DevTables& tb, int nb, int nblk, const S* B, double alpha,
+                               double beta, const S* x, S* y, cudaStream_t st);
+cudaError_t stream_rows_error(int* flag, bool reset);  // bounded-wait expiry flag of those kernels
+// BN = -c J_off Ainv_nbr and BT = (-c Ainv_nbr J_off,nbr)^T (3 blocks per element each; BT may
+// be null): the block-Jacobi preconditioner folded into the stage operator.
+template <class S>
+cudaError_t launch_fold_blocks(const DevMesh& m, int nb, const S* J, const S* Ainv, double c, S* BN, S* BT,
+                               cudaStream_t st);
 int reduction_blocks();  // number of partial sums used by the reductions
 
 }  // namespace pp

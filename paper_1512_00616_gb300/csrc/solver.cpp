@@ -3,9 +3,10 @@
 // Only Krylov scalars (Hessenberg column, norms) cross to the host.
 //
 //  - gmres():          restarted, right-preconditioned GMRES with classical
-//                      Gram-Schmidt applied twice (fused update + multi-dot
-//                      kernels), Givens rotations on the host.  Used for the
-//                      stage solves (block-Jacobi preconditioned) and, without
+//                      Gram-Schmidt and selective reorthogonalization (fused
+//                      update + multi-dot kernels), Givens rotations on the
+//                      device.  Used for the stage solves (on the operator with
+//                      the block-Jacobi preconditioner folded in) and, without
 //                      preconditioner, for the shooting system (Algorithm primal)
 //                      and the periodic adjoint system (Algorithm dual).
 //  - primal_sweep():   Eq. dirk2: DIRK3 steps, Newton per stage on
@@ -23,6 +24,8 @@
 #include <functional>
 
 #include "context.h"
+#include "prof.h"
+#include "../../include/pp_prof.h"
 
 namespace pp {
 
@@ -50,6 +53,14 @@ int host_norm(pp_ctx* ctx, int64_t n, const double* x, double* out) {
   PP_TRY(host_dot<double>(ctx, n, x, x, &d));
   *out = std::sqrt(d);
   if (!std::isfinite(*out)) return set_error(ctx, PP_ENAN, "non-finite norm");
+  return PP_OK;
+}
+
+// Bounded-wait expiry in the TMA-staged block-row kernels (checked at sweep ends).
+int check_stream_kernels(pp_ctx* ctx) {
+  int flag = 0;
+  PP_CK(stream_rows_error(&flag, true));
+  if (flag) return set_error(ctx, PP_ECUDA, "block-row kernel: shared-memory pipeline wait expired");
   return PP_OK;
 }
 
@@ -119,10 +130,8 @@ int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const
         z = zj;
       }
       PP_TRY(A(z, K.w));
-      PP_CK(launch_mdot<S>(n, K.V, n, j + 1, K.w, d_h1, ctx->d_partial, ctx->d_counter, ctx->stream));
-      PP_CK(launch_update_mdot<S>(n, K.V, n, j + 1, d_h1, K.w, d_h2, ctx->d_partial, ctx->d_counter, ctx->stream));
-      PP_CK(launch_update_norm2_givens<S>(n, K.V, n, j + 1, d_h2, K.w, d_nrm, ctx->d_partial, ctx->d_counter, j, m,
-                                          d_h1, d_h2, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
+      PP_CK(launch_arnoldi_ortho<S>(n, K.V, n, j + 1, K.w, d_h1, d_h2, d_nrm, ctx->d_partial, ctx->d_counter, j, m,
+                                    K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
       double* slot = K.h_h + 8 * (j % kRing);
       PP_CK(cudaMemcpyAsync(slot, K.d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
@@ -177,12 +186,30 @@ struct StageView {
   const float* JT32 = nullptr;
   const float* A32 = nullptr;
   const float* AT32 = nullptr;
+  const double* BN = nullptr;     // folded operator I + BN = (M - cJ) D^{-1} (optional, FP64 mode)
+  const double* BT = nullptr;     // folded transposed operator I + BT = (M - cJ)^T D^{-T}
+  const float* BN32 = nullptr;    // mixed mode: FP32 folded blocks of the inner solves
+  const float* BT32 = nullptr;
 };
 
 // FP32 GMRES on the FP32 stage operator (block-Jacobi FP32 preconditioner), b and x FP32.
 int stage_solve32(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans, const float* b, float* x,
                   double rtol, int maxit, int* iters) {
   const DevMesh& m = mesh->dev;
+  const float* Bf = trans ? sv.BT32 : sv.BN32;
+  if (Bf) {
+    // folded operator: GMRES on (I + B) y = b, then x = D^{-1} y (D^{-T} y)
+    float* yv = ctx->k32.t;
+    OpT<float> A = [&](const float* in, float* out) {
+      ProfScope ps(PP_K_STAGE_OP32, ctx->stream);
+      PP_CK(launch_stream_rows<float>(m, ctx->tb, ctx->tb.nb, 3, Bf, 0.0, 1.0, in, out, ctx->stream));
+      return PP_OK;
+    };
+    int st = gmres<float>(ctx, ctx->k32, A, OpT<float>(), b, yv, rtol, 0.0, maxit, iters, nullptr);
+    if (st != PP_OK && st != PP_ENOCONV) return st;
+    PP_CK(launch_block_apply<float>(m, ctx->tb.nb, trans ? sv.AT32 : sv.A32, yv, x, 0, ctx->stream));
+    return PP_OK;  // an inexact inner / Newton solve is acceptable
+  }
   const float* Jm = trans ? sv.JT32 : sv.J32;   // the transposed copies run through the normal kernels
   const float* Am = trans ? sv.AT32 : sv.A32;
   OpT<float> A = [&](const float* in, float* out) {
@@ -235,6 +262,23 @@ int stage_solve(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans
     if (st == PP_ENOCONV) return set_error(ctx, PP_ENOCONV, "stage FGMRES hit gmres_maxit");
     return st;
   }
+  // FP64 path with the folded operator: GMRES on (I + B) y = b, then x = D^{-1} y (D^{-T} y)
+  const double* Bf = trans ? sv.BT : sv.BN;
+  if (Bf) {
+    double* yv = ctx->kin.t;  // unused by GMRES without a preconditioner
+    Op A = [&](const double* in, double* out) {
+      ProfScope ps(PP_K_STAGE_OP, ctx->stream);
+      PP_CK(launch_stream_rows<double>(m, ctx->tb, ctx->tb.nb, 3, Bf, 0.0, 1.0, in, out, ctx->stream));
+      return PP_OK;
+    };
+    int st = gmres<double>(ctx, ctx->kin, A, Op(), b, yv, rtol, atol, ctx->cfg.gmres_maxit, iters, nullptr);
+    if (st != PP_OK && st != PP_ENOCONV) return st;
+    if (!trans) PP_CK(launch_block_apply<double>(m, ctx->tb.nb, sv.Ainv, yv, x, 0, ctx->stream));
+    else if (sv.AinvT) PP_CK(launch_block_apply<double>(m, ctx->tb.nb, sv.AinvT, yv, x, 0, ctx->stream));
+    else PP_CK(launch_block_apply<double>(m, ctx->tb.nb, sv.Ainv, yv, x, 1, ctx->stream));
+    if (st == PP_ENOCONV && exact) return set_error(ctx, PP_ENOCONV, "stage GMRES hit gmres_maxit");
+    return PP_OK;
+  }
   // FP64 path: with stored transposes the transposed system uses the normal (row-streaming) kernels
   const bool useT = trans && sv.JT && sv.AinvT;
   const double* Jm = useT ? sv.JT : sv.J;
@@ -263,6 +307,10 @@ StageView stage_view_slot(pp_ctx* ctx, size_t s, double c) {
   StageView v{ctx->st_J + s * ne * 4 * nb2(ctx), ctx->st_Ainv ? ctx->st_Ainv + s * ne * nb2(ctx) : nullptr, c};
   if (ctx->st_JT) v.JT = ctx->st_JT + s * ne * 4 * nb2(ctx);
   if (ctx->st_AinvT) v.AinvT = ctx->st_AinvT + s * ne * nb2(ctx);
+  if (ctx->st_BN) v.BN = ctx->st_BN + s * ne * 3 * nb2(ctx);
+  if (ctx->st_BT) v.BT = ctx->st_BT + s * ne * 3 * nb2(ctx);
+  if (ctx->st_BN32) v.BN32 = ctx->st_BN32 + s * ne * 3 * nb2(ctx);
+  if (ctx->st_BT32) v.BT32 = ctx->st_BT32 + s * ne * 3 * nb2(ctx);
   if (ctx->st_J32) {
     v.J32 = ctx->st_J32 + s * ne * 4 * nb2(ctx);
     v.JT32 = ctx->st_JT32 + s * ne * 4 * nb2(ctx);
@@ -294,12 +342,18 @@ int finalize_stage_slot(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, b
       PP_CK(launch_transpose_blocks<double, float>(m, nb, sv.J, const_cast<float*>(sv.JT32), ctx->stream));
       if (sv.JT) PP_CK(launch_transpose_blocks<double, double>(m, nb, sv.J, const_cast<double*>(sv.JT), ctx->stream));
     }
+    if (sv.BN32)
+      PP_CK(launch_fold_blocks<float>(m, nb, sv.J32, sv.A32, sv.c, const_cast<float*>(sv.BN32),
+                                      full && sv.BT32 ? const_cast<float*>(sv.BT32) : nullptr, ctx->stream));
     return PP_OK;
   }
   PP_CK(launch_block_inverse<double>(m, ctx->tb, sv.J, sv.c, const_cast<double*>(sv.Ainv),
                                      full ? const_cast<double*>(sv.AinvT) : nullptr, ctx->d_status, ctx->stream));
   if (full && sv.JT)
     PP_CK(launch_transpose_blocks<double, double>(m, nb, sv.J, const_cast<double*>(sv.JT), ctx->stream));
+  if (sv.BN)
+    PP_CK(launch_fold_blocks(m, nb, sv.J, sv.Ainv, sv.c, const_cast<double*>(sv.BN),
+                             full && sv.BT ? const_cast<double*>(sv.BT) : nullptr, ctx->stream));
   return PP_OK;
 }
 
@@ -493,6 +547,7 @@ int primal_sweep(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, c
   }
   if (u_final) PP_TRY(copy(ctx, n, u_final, u));
   PP_CK(cudaStreamSynchronize(ctx->stream));
+  PP_TRY(check_stream_kernels(ctx));
   ctx->lin_valid = true;
   return PP_OK;
 }
@@ -533,6 +588,7 @@ int tangent_sweep(pp_ctx* ctx, const double* v, double* out) {
   }
   PP_TRY(lincomb(ctx, n, out, {1.0, -1.0}, {v0, du}));
   PP_CK(cudaStreamSynchronize(ctx->stream));
+  PP_TRY(check_stream_kernels(ctx));
   return PP_OK;
 }
 
@@ -628,6 +684,7 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
   }
   PP_TRY(copy(ctx, n, lam0, lam));
   PP_CK(cudaStreamSynchronize(ctx->stream));
+  PP_TRY(check_stream_kernels(ctx));
   if (dFdmu)
     for (int j = 0; j < n_mu; ++j) dFdmu[j] = withF ? grad[j] : 0.0;
   return PP_OK;

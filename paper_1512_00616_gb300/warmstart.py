@@ -273,14 +273,54 @@ def experiment(config="c0", n_train=96, n_test=16, tol=1e-8, epochs=6000, seed=4
                 mean=agg)
 
 
+def cold_time_to_gradient(config="c1", n_test=1, tol=1e-8, seed=45):
+    """Time to a periodic gradient from the steady-state cold start, plain FP64 against
+    mixed precision, on held-out mu of the +-20% box (no network: for workloads where
+    generating a training set does not fit the available GPU time)."""
+    from pp_inputs import CONFIGS, KIN_FOURIER6, MU_F6_BASE, MU_F6_SCALE, config_mesh
+    c = CONFIGS[config]
+    mesh = config_mesh(config)
+    T = 5.0
+    lo, hi = MU_F6_BASE - 0.2 * MU_F6_SCALE, MU_F6_BASE + 0.2 * MU_F6_SCALE
+    test = lhs(n_test, lo, hi, seed)
+    w = np.array([-1.0 / T, 0.0])  # F = J_E
+    rows = []
+    grads = {}
+    for name, prec in (("fp64", A.PP_PREC_FP64), ("mixed", A.PP_PREC_MIXED)):
+        ctx = A.pp_create(A.pp_config_default(p=c["p"], kin=KIN_FOURIER6, precision=prec, adj_tol=1e-10))
+        m = A.pp_mesh_create(ctx, mesh.verts, mesh.tris, mesh.ftag)
+        for i, mu in enumerate(test):
+            t0 = time.perf_counter()
+            _, _, st, _, _ = shoot_with_warm_start(ctx, m, mu, c["Nt"], tol)
+            t1 = time.perf_counter()
+            F, g, ast = A.pp_periodic_adjoint(ctx, m, mu, c["Nt"], w)
+            t2 = time.perf_counter()
+            grads[(name, i)] = g
+            rows.append(dict(precision=name, mu=i, newton=st["newton_iters"], tangent_sweeps=st["krylov_iters"],
+                             periodicity=st["residual"][-1], shoot_s=t1 - t0, adjoint_s=t2 - t1,
+                             total_s=t2 - t0, J_E=F))
+        A.pp_mesh_destroy(m)
+        A.pp_destroy(ctx)
+    for r in rows:
+        if r["precision"] == "mixed":
+            ga, gb = grads[("fp64", r["mu"])], grads[("mixed", r["mu"])]
+            r["grad_rel_diff_vs_fp64"] = float(np.linalg.norm(gb - ga) / np.linalg.norm(ga))
+    return dict(config=config, tol=tol, rows=rows)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", default="c0")
     ap.add_argument("--train", type=int, default=96)
     ap.add_argument("--test", type=int, default=16)
     ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--cold-only", action="store_true",
+                    help="plain FP64 against mixed precision from the cold start, no network")
     a = ap.parse_args()
-    print(json.dumps(experiment(a.config, a.train, a.test, epochs=a.epochs)))
+    if a.cold_only:
+        print(json.dumps(cold_time_to_gradient(a.config, a.test)))
+    else:
+        print(json.dumps(experiment(a.config, a.train, a.test, epochs=a.epochs)))
 
 
 if __name__ == "__main__":
