@@ -25,6 +25,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) per launch of a kernel class on a workload, from one ncu
+# capture of the current kernel (profiles/ names the capture); absent -> null.
+MEASURED_TRAFFIC = {}
+
 METRIC = "DOF*stages/s fwd+adjoint"
 UNIT = "DOF*stages/s"
 
@@ -221,7 +225,7 @@ def run_ours(args, rank, world, local_rank):
     ms = float(tmax.item())
     A.pp_mesh_destroy(m)
     A.pp_destroy(ctx)
-    return dict(ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, split=split, kern_launches=launches_k, kern_ms=kern_ms,
+    return dict(config=args.config, ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, split=split, kern_launches=launches_k, kern_ms=kern_ms,
                 counts=counts, e2e=e2e)
 
 
@@ -245,7 +249,8 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c):
         flops = ne * 16 * 2 * (w_fma + j_fma)
         ach = flops / t / 1e12
         return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
-                "frac": ach / fp64_tflops if fp64_tflops else None, "traffic": None,
+                "frac": ach / fp64_tflops if fp64_tflops else None,
+                "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
                 "kernel": "k_jacobian", "launches": res["kern_launches"], "avg_us": t * 1e6}
     if kernel in ("stage_matvec", "block_apply", "stage_matvec32", "block_apply32", "stage_op", "stage_op32"):
         blocks = 4 if kernel.startswith("stage_matvec") else (3 if kernel.startswith("stage_op") else 1)
@@ -259,13 +264,14 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c):
             flops = 2.0 * ne * blocks * nb * nb
             ach = flops / t / 1e12
             return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
-                    "frac": ach / fp64_tflops if fp64_tflops else None, "traffic": None,
+                    "frac": ach / fp64_tflops if fp64_tflops else None,
+                    "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
                     "kernel": ("k_stream_rows<%d,3,double> (I + B, folded block-Jacobi)" % nb if kernel == "stage_op"
                                else "k_" + kernel.replace("32", "") + "<double>"), "launches": res["kern_launches"],
                     "avg_us": t * 1e6, "hbm_gbs_equiv": byts / t / 1e9}
         ach = byts / t / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "frac": ach / peaks["hbm_gbs"], "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
                 "kernel": ("k_stream_rows<%d,3,float> (I + B, folded block-Jacobi)" % nb if kernel == "stage_op32"
                            else "k_" + kernel.replace("32", "") + "<float>"),
                 "launches": res["kern_launches"], "avg_us": t * 1e6}
@@ -333,7 +339,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
         "config": {"workload": workload, "precision": args.precision, "dof": res["nu"], "elements": res["ne"], "Nt": res["Nt"],
                    "parallelism": f"replicas x{world}",
-                   "l2": "working set (stored stage Jacobians, ~40 GB) far larger than L2; no flush needed"},
+                   "l2": "working set (stored stage linearization, ~126 GB in FP64) far larger than L2; no flush needed"},
         "roofline": roof, "fp64_fma_peak_tflops_measured": fp64,
         "clocks": res["clocks"],
         "gpu_launches": int(sum(res["counts"].values())),

@@ -598,9 +598,12 @@ __device__ __forceinline__ void cta_reduce(S* v, int kb, double* bp, int j0) {
 }
 
 // Grid level of the reduction of the CTA partials bp[0..nk).  Returns true in the one
-// CTA that holds the final sums in out[] (the last CTA to arrive).
+// CTA that holds the final sums in out[] (the last CTA to arrive).  The last CTA splits
+// the partial rows into CGS_T / nk' chunks per output, loads each chunk with all loads
+// in flight, and sums the chunk totals in chunk order (a fixed order: reproducible).
 __device__ __forceinline__ bool cgs_finish(int nk, const double* bp, double* partial, unsigned* counter,
                                            double* out) {
+  __shared__ double chunk[CGS_T];
   for (int t = threadIdx.x; t < nk; t += CGS_T) partial[(size_t)blockIdx.x * nk + t] = bp[t];
   __shared__ bool last;
   __threadfence();
@@ -609,20 +612,31 @@ __device__ __forceinline__ bool cgs_finish(int nk, const double* bp, double* par
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = gridDim.x;
-  for (int j = warp; j < nk; j += CGS_T / 32) {
-    double s0 = 0.0, s1 = 0.0;
-    int b = lane;
-    for (; b + 32 < nb; b += 64) {
-      s0 += __ldcg(partial + (size_t)b * nk + j);
-      s1 += __ldcg(partial + (size_t)(b + 32) * nk + j);
-    }
-    if (b < nb) s0 += __ldcg(partial + (size_t)b * nk + j);
-    double s = s0 + s1;
+  int nc = CGS_T / nk;  // chunks per output
+  if (nc > 32) nc = 32;
+  if (nc > nb) nc = nb;
+  if (nc < 1) nc = 1;
+  const int per = (nb + nc - 1) / nc;
+  for (int t = threadIdx.x; t < nk * nc; t += CGS_T) {
+    const int j = t / nc, c = t - j * nc;
+    const int b0 = c * per, b1 = min(nb, b0 + per);
+    double a[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[j] = s;
+    for (int r = 0; r < 8; ++r) a[r] = 0.0;
+    int b = b0;
+    for (; b + 7 < b1; b += 8) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) a[r] += __ldcg(partial + (size_t)(b + r) * nk + j);
+    }
+    for (; b < b1; ++b) a[0] += __ldcg(partial + (size_t)b * nk + j);
+    chunk[t] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nk; j += CGS_T) {
+    double s = 0.0;
+    for (int c = 0; c < nc; ++c) s += chunk[j * nc + c];
+    out[j] = s;
   }
   if (threadIdx.x == 0) *counter = 0u;
   __syncthreads();

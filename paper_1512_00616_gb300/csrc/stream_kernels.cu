@@ -119,7 +119,8 @@ struct StreamShape {
   static constexpr int THREADS = 32 * (CW + 1);
   static constexpr int UNIT = NB * NB + 2 * NB;  // block + input slice (+ own slice), elements of S
   static constexpr int UNIT_BYTES = UNIT * (int)sizeof(S);
-  static constexpr int BUDGET = 50 * 1024;  // several CTAs per SM where the units fit
+  static constexpr int BUDGET = 100 * 1024;  // two CTAs per SM where the units fit (measured
+                                             // faster than four smaller rings at nb = 40)
   static constexpr int R = (BUDGET / UNIT_BYTES) > NBLK + 1 ? (BUDGET / UNIT_BYTES) : NBLK + 1;
   static constexpr int RED_BYTES = NG * NB * (int)sizeof(S);
   static constexpr int SMEM = R * UNIT_BYTES + RED_BYTES + 2 * R * 8 + R * 4;
