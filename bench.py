@@ -137,6 +137,23 @@ def _threads():
 
 
 # --------------------------------------------------------------------------- ours
+def max_over_ranks(x, device="cpu"):
+    """Largest x over the ranks of the default process group (x itself without one).
+    Each rank is an independent replica; the slowest one sets the job's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, ms_max, world):
+    """Units all ranks processed (the same per rank: weak scaling) per second of the slowest rank."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -222,10 +239,9 @@ def run_ours(args, rank, world, local_rank):
             e2e_ms = e0.elapsed_time(e1) / args.steps
             e2e = dict(ms_per_step=e2e_ms, h2d=nu * 8, d2h=nu * 8 + 8 * len(mu))
 
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-    ms = float(tmax.item())
+    ms = max_over_ranks(ms, dev)
+    if e2e is not None:
+        e2e["ms_per_step"] = max_over_ranks(e2e["ms_per_step"], dev)
     A.pp_mesh_destroy(m)
     A.pp_destroy(ctx)
     return dict(config=args.config, ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, split=split, kern_launches=launches_k, kern_ms=kern_ms,
@@ -334,7 +350,7 @@ def main():
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
     fp64 = A.pp_measure_fp64_peak(local_rank)
     units = res["nu"] * res["Nt"] * 3
-    value = units / (res["ms"] * 1e-3) * world
+    value = whole_job_value(units, res["ms"], world)
     roof = roofline_for(args.roofline_kernel, res, peaks, fp64, c)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -352,7 +368,7 @@ def main():
     }
     if res["e2e"]:
         e = res["e2e"]
-        line["e2e"] = {"value": units / (e["ms_per_step"] * 1e-3) * world, "unit": UNIT,
+        line["e2e"] = {"value": whole_job_value(units, e["ms_per_step"], world), "unit": UNIT,
                        "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
     if not args.no_cpu_baseline and world == 1:
         s = oracle_sample(args.config, args.cpu_budget)
