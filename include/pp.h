@@ -102,8 +102,12 @@ typedef struct pp_config {
 void pp_config_default(pp_config* cfg);
 
 /* Creates a context on cfg->device.  The context owns all device workspace,
-   including the stored linearization (stage states, element block Jacobians
-   and their block-LU factors, kept in HBM for the whole period).
+   including the stored linearization of a period (allocated by the first sweep):
+   per stage the stage state, the element block Jacobians, the explicit inverses of
+   the stage diagonal blocks and, while 8 GB of device memory stay free, the stage
+   operator with the block-Jacobi preconditioner folded in (normal and transposed)
+   and transposed Jacobian copies.  About 420 MB per stage for 2048 elements at p = 3
+   in FP64; with checkpoint_stride K only one K-step segment of stages is kept.
    Errors: PP_EINVAL (p out of range, null pointers), PP_ECUDA. */
 int pp_create(const pp_config* cfg, pp_ctx** out);
 int pp_destroy(pp_ctx* ctx);
@@ -164,9 +168,11 @@ int pp_qoi_rate_noalloc(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int 
    [(Nt+1)][N_u] or NULL.  u_final: DEVICE [N_u] or NULL.  qoi: HOST [4] or NULL:
    (W, J_x, J_E = -W/T, J_T = -J_x/T), W and J_x the solver-consistent
    discrete work and x-impulse (Eqs. qoi, qoi-disc).
-   The call stores the linearization (stage states, block Jacobians, LU
-   factors) used by pp_tangent_matvec, pp_adjoint_sweep and
-   pp_periodic_adjoint.  Errors: PP_ENOCONV (stage Newton cap), PP_ENAN. */
+   The call stores the linearization (stage states, block Jacobians, block-Jacobi
+   inverses, folded stage operators; or state checkpoints, see checkpoint_stride)
+   used by pp_tangent_matvec, pp_adjoint_sweep and pp_periodic_adjoint.
+   Errors: PP_ENOCONV (stage Newton cap), PP_ENAN, PP_ENOMEM (storage), PP_ECUDA
+   (including an expired wait in the shared-memory pipeline of the block-row kernels). */
 int pp_primal_period(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
                      double* u_traj, double* u_final, double* qoi);
 
