@@ -1,0 +1,178 @@
+"""ALE DG residual for the rigid-plus-blended mesh motion with a discrete geometric
+conservation law (oracle; test infrastructure only).
+
+The map x(X, t) of oracle/blend.py is interpolated nodally in each element's degree-p
+space (x_h, v_h), so that the cofactor matrix C = g_h G_h^{-1} of G_h = grad_X x_h is a
+polynomial and C N is continuous across faces (the interpolant is conforming).  The
+unknown is U_X = gbar U on the reference domain, with
+
+    M dU_X/dt = r(U_X) = int grad_X phi . C (F(U, grad_x U) - U (x) v_h) dX
+                         - sum_faces int phi |C^T N| H(U-, U+, n, v_h . n) dS_X,
+
+U = U_X / gbar, grad_x U = G_h^{-T} grad_X U, n = C^T N / |C^T N| (Nanson), and the
+numerical flux H of the rigid oracle.  gbar is the discrete GCL field,
+
+    M dgbar/dt = -D[C v_h],   D[f] = int grad_X phi . f dX - sum_faces int phi f . N dS_X,
+
+integrated by the same DIRK as the flow.  Because D[C] = 0 exactly (Piola identity of
+the polynomial map, integrated exactly), r(gbar U_inf) = -U_inf D[C v_h] for any gbar,
+so a uniform flow stays uniform through every DIRK stage.  With b = 1 everywhere the
+residual is the rigid one (G = Q, g = 1, gbar = 1).
+
+Readings kept from the rigid oracle: fluxes, boundary states and the penalty (sigma on
+the reference face length), mass matrix of the reference element.
+"""
+import numpy as np
+
+from . import blend
+from .dg import DG, KIN_HEAVE_PITCH, inviscid_flux, normal_flux, roe_flux, viscous_flux
+
+
+class BlendedDG(DG):
+    def __init__(self, mesh, p, r1=2.0, r2=8.0, **kw):
+        super().__init__(mesh, p, **kw)
+        self.r1, self.r2 = r1, r2
+        xi_n = self.basis.nodes                                              # [Np, 2]
+        self.Xn = self.X0[:, None, :] + np.einsum("edk,jk->ejd", self.B, xi_n)   # [Ne, Np, 2]
+        self.Minv_ref = np.linalg.inv(self.Mref)
+
+    # ------------------------------------------------------------------ kinematics
+    def heave(self, mu, t):
+        w = self.omega
+        if self.kin == KIN_HEAVE_PITCH:
+            return mu[0] * np.sin(w * t)
+        return mu[0] * np.sin(w * t) + mu[1] * np.cos(w * t) + mu[2] * np.sin(2 * w * t)
+
+    def nodal_map(self, mu, t):
+        """x and v_X of the blended map at the element nodes, [Ne, Np, 2] each."""
+        th, thd, hd = self.motion(mu, t)
+        x, _, _, _, v = blend.blended_map(self.Xn, self.heave(mu, t), th, hd, thd, self.r1, self.r2)
+        return x, v
+
+    def _geom(self, xn, vn, phi, dphi):
+        """G_h, cofactor C = g G^{-1}, G^{-T} and v_h at points with basis values phi
+        [nq, Np] and reference gradients dphi [nq, Np, 2] (per element)."""
+        gradX = np.einsum("ekl,qjl->eqjk", self.BinvT, dphi)                # grad_X phi_j [Ne, nq, Np, 2]
+        return self._geom_pts(xn, vn, np.broadcast_to(phi, (self.Ne,) + phi.shape), gradX)
+
+    @staticmethod
+    def _geom_pts(xn, vn, phi, gradX):
+        """As _geom with per-element basis values phi [Ne, nq, Np] and gradients gradX."""
+        G = np.einsum("eji,eqjk->eqik", xn, gradX)                          # dx_i / dX_k
+        g = G[..., 0, 0] * G[..., 1, 1] - G[..., 0, 1] * G[..., 1, 0]
+        C = np.stack([np.stack([G[..., 1, 1], -G[..., 0, 1]], -1),
+                      np.stack([-G[..., 1, 0], G[..., 0, 0]], -1)], -2)     # g G^{-1}
+        GinvT = np.swapaxes(C, -1, -2) / g[..., None, None]
+        v = np.einsum("eqj,eji->eqi", phi, vn)
+        return G, g, C, GinvT, v, gradX
+
+    # ------------------------------------------------------------------ GCL
+    def gcl_rhs(self, mu, t):
+        """-D[C v_h] per element node [Ne, Np] (right-hand side of M dgbar/dt)."""
+        xn, vn = self.nodal_map(mu, t)
+        _, _, C, _, v, gradX = self._geom(xn, vn, self.phi_v, self.dphi_v)
+        Cv = np.einsum("eqJi,eqi->eqJ", C, v)
+        wq = self.w_v[None, :] * self.detB[:, None]
+        D = np.einsum("eq,eqjJ,eqJ->ej", wq, gradX, Cv)
+        for f in range(3):
+            _, _, Cf, _, vf, _ = self._geom(xn, vn, self.phi_f[f], self.dphi_f[f])
+            CvN = np.einsum("eqJi,eqi,eJ->eq", Cf, vf, self.N[:, f])
+            D = D - np.einsum("q,e,qj,eq->ej", self.w_f, self.L[:, f], self.phi_f[f], CvN)
+        return -D
+
+    def gcl_rate(self, mu, t):
+        """dgbar/dt = M^{-1}(-D[C v_h]) per element [Ne, Np]."""
+        return np.einsum("ij,ej->ei", self.Minv_ref, self.gcl_rhs(mu, t)) / self.detB[:, None]
+
+    def geometric_g(self, mu, t):
+        """g_h of the interpolated map at the element nodes [Ne, Np] (the initial gbar)."""
+        xn, vn = self.nodal_map(mu, t)
+        return self._geom(xn, vn, np.eye(self.Np), self.basis.dphi(self.basis.nodes))[1]
+
+    # ------------------------------------------------------------------ residual
+    def residual_blended(self, uX, mu, t, gbar):
+        """r(U_X) [.., Ne, 4, Np] for nodal U_X [.., Ne, 4, Np] and gbar [Ne, Np]."""
+        gam, mu_v, Pr = self.gam, self.mu_visc, self.Pr
+        xn, vn = self.nodal_map(mu, t)
+        uN = uX[..., self.nbr_safe, :, :]
+        gN = gbar[self.nbr_safe]
+
+        def state(u, gb, phi, gradX):
+            UX = np.einsum("...eai,eqi->...eqa", u, phi)
+            gq = np.einsum("ei,eqi->eq", gb, phi)
+            dUX = np.einsum("...eai,eqid->...eqad", u, gradX)
+            dg = np.einsum("ei,eqid->eqd", gb, gradX)
+            U = UX / gq[..., None]
+            dU = (dUX - U[..., None] * dg[..., None, :]) / gq[..., None, None]   # grad_X U
+            return U, dU
+
+        # volume
+        G, g, C, GinvT, v, gradX = self._geom(xn, vn, self.phi_v, self.dphi_v)
+        phi_e = np.broadcast_to(self.phi_v, (self.Ne,) + self.phi_v.shape)
+        U, dUX = state(uX, gbar, phi_e, gradX)
+        dU = np.einsum("eqik,...eqak->...eqai", GinvT, dUX)                    # grad_x U
+        Ftot = inviscid_flux(U, gam) - U[..., None] * v[..., None, :] - viscous_flux(U, dU, mu_v, Pr, gam)
+        FX = np.einsum("eqJi,...eqai->...eqaJ", C, Ftot)
+        wq = self.w_v[None, :] * self.detB[:, None]
+        r = np.einsum("eq,eqjJ,...eqaJ->...eaj", wq, gradX, FX)
+        # faces
+        for f in range(3):
+            H = self.face_flux_blended(uX, uN, gbar, gN, f, xn, vn)
+            r = r - np.einsum("q,e,qj,...eqa->...eaj", self.w_f, self.L[:, f], self.phi_f[f], H)
+        return r
+
+    def face_flux_blended(self, uX, uN, gbar, gN, f, xn, vn):
+        """Reference-face numerical flux |C^T N| H at the points of local face f
+        [.., Ne, nqf, 4] (outward from the element, per unit reference length)."""
+        gam, mu_v, Pr = self.gam, self.mu_visc, self.Pr
+
+        def state(u, gb, phi, gradX):
+            UX = np.einsum("...eai,eqi->...eqa", u, phi)
+            gq = np.einsum("ei,eqi->eq", gb, phi)
+            dUX = np.einsum("...eai,eqid->...eqad", u, gradX)
+            dg = np.einsum("ei,eqid->eqd", gb, gradX)
+            U = UX / gq[..., None]
+            return U, (dUX - U[..., None] * dg[..., None, :]) / gq[..., None, None]
+
+        Gf, gf, Cf, GinvTf, vf, gradXf = self._geom(xn, vn, self.phi_f[f], self.dphi_f[f])
+        phi_m = np.broadcast_to(self.phi_f[f], (self.Ne,) + self.phi_f[f].shape)
+        Um, dUXm = state(uX, gbar, phi_m, gradXf)
+        dUm = np.einsum("eqik,...eqak->...eqai", GinvTf, dUXm)
+        # neighbour trace at the matched points, with the neighbour's own map (the
+        # interpolated map is continuous across the face, its gradient is not)
+        gradXn = np.einsum("ekl,eqjl->eqjk", self.BinvT_nbr[:, f], self.dphiN[:, f])
+        nb = self.nbr_safe[:, f]
+        GinvTp = self._geom_pts(xn[nb], vn[nb], self.phiN[:, f], gradXn)[3]
+        Up, dUXp = state(uN[..., f, :, :], gN[:, f], self.phiN[:, f], gradXn)
+        dUp = np.einsum("eqik,...eqak->...eqai", GinvTp, dUXp)
+        nt = np.einsum("eqJi,eJ->eqi", Cf, self.N[:, f])                      # C^T N
+        ln = np.sqrt(nt[..., 0] ** 2 + nt[..., 1] ** 2)
+        n = nt / ln[..., None]
+        vnrm = vf[..., 0] * n[..., 0] + vf[..., 1] * n[..., 1]
+        sig = self.sigma[:, f][:, None, None]
+        Fvm = viscous_flux(Um, dUm, mu_v, Pr, gam)
+        Fvp = viscous_flux(Up, dUp, mu_v, Pr, gam)
+
+        def dn(F):
+            return F[..., 0] * n[..., None, 0] + F[..., 1] * n[..., None, 1]
+
+        H_int = roe_flux(Um, Up, n, vnrm, gam) - (0.5 * dn(Fvm + Fvp) + sig * (Up - Um))
+        Uinf = np.broadcast_to(self.Uinf, Um.shape) + 0.0 * Um
+        H_far = roe_flux(Um, Uinf, n, vnrm, gam) - (dn(Fvm) + sig * (Uinf - Um))
+        rho = Um[..., 0]
+        e_int = Um[..., 3] / rho - 0.5 * (Um[..., 1] ** 2 + Um[..., 2] ** 2) / rho**2
+        vb = vf + 0.0 * rho[..., None]
+        Ub = np.stack([rho, rho * vb[..., 0], rho * vb[..., 1],
+                       rho * (e_int + 0.5 * (vb[..., 0] ** 2 + vb[..., 1] ** 2))], -1)
+        H_wall = normal_flux(Ub, n, vnrm, gam) - (dn(viscous_flux(Ub, dUm, mu_v, Pr, gam, adiabatic=True))
+                                                   + sig * (Ub - Um))
+        tag = self.tag[:, f][:, None, None]
+        return np.where(tag == 0, H_int, np.where(tag == 1, H_wall, H_far)) * ln[..., None]
+
+    def gbar_dirk(self, mu, t0, dt, g0, tableau):
+        """gbar at the stages and at the end of one DIRK step from gbar(t0) = g0: the GCL
+        rate does not depend on gbar, so every stage value is explicit."""
+        A, b, c = tableau
+        k = [self.gcl_rate(mu, t0 + c[i] * dt) for i in range(len(b))]
+        stages = [g0 + dt * sum(A[i][j] * k[j] for j in range(i + 1)) for i in range(len(b))]
+        return stages, g0 + dt * sum(b[i] * k[i] for i in range(len(b)))
