@@ -25,7 +25,7 @@ the reference face length), mass matrix of the reference element.
 import numpy as np
 
 from . import blend
-from .dg import DG, KIN_HEAVE_PITCH, inviscid_flux, normal_flux, roe_flux, viscous_flux
+from .dg import CS_STEP, DG, KIN_HEAVE_PITCH, inviscid_flux, normal_flux, roe_flux, viscous_flux
 
 
 class BlendedDG(DG):
@@ -44,7 +44,13 @@ class BlendedDG(DG):
         return mu[0] * np.sin(w * t) + mu[1] * np.cos(w * t) + mu[2] * np.sin(2 * w * t)
 
     def nodal_map(self, mu, t):
-        """x and v_X of the blended map at the element nodes, [Ne, Np, 2] each."""
+        """x and v_X of the blended map at the element nodes, [Ne, Np, 2] each.  t = None:
+        the t = 0 pose with the mesh at rest (the steady-state problem)."""
+        if t is None:
+            th, _, _ = self.motion(mu, 0.0)
+            x, _, _, _, v = blend.blended_map(self.Xn, self.heave(mu, 0.0), th, 0.0 * th, 0.0 * th,
+                                              self.r1, self.r2)
+            return x, 0.0 * v
         th, thd, hd = self.motion(mu, t)
         x, _, _, _, v = blend.blended_map(self.Xn, self.heave(mu, t), th, hd, thd, self.r1, self.r2)
         return x, v
@@ -85,16 +91,21 @@ class BlendedDG(DG):
         return np.einsum("ij,ej->ei", self.Minv_ref, self.gcl_rhs(mu, t)) / self.detB[:, None]
 
     def geometric_g(self, mu, t):
-        """g_h of the interpolated map at the element nodes [Ne, Np] (the initial gbar)."""
+        """g_h of the interpolated map at the element nodes [Ne, Np] (the initial gbar);
+        t = None: the frozen t = 0 pose."""
         xn, vn = self.nodal_map(mu, t)
         return self._geom(xn, vn, np.eye(self.Np), self.basis.dphi(self.basis.nodes))[1]
 
     # ------------------------------------------------------------------ residual
     def residual_blended(self, uX, mu, t, gbar):
         """r(U_X) [.., Ne, 4, Np] for nodal U_X [.., Ne, 4, Np] and gbar [Ne, Np]."""
+        return self.residual_blended_local(uX, uX[..., self.nbr_safe, :, :], mu, t, gbar)
+
+    def residual_blended_local(self, uX, uN, mu, t, gbar):
+        """As residual_blended with the face-neighbour states uN [.., Ne, 3, 4, Np] given
+        separately (for block Jacobians by the complex step)."""
         gam, mu_v, Pr = self.gam, self.mu_visc, self.Pr
         xn, vn = self.nodal_map(mu, t)
-        uN = uX[..., self.nbr_safe, :, :]
         gN = gbar[self.nbr_safe]
 
         def state(u, gb, phi, gradX):
@@ -168,6 +179,86 @@ class BlendedDG(DG):
                                                    + sig * (Ub - Um))
         tag = self.tag[:, f][:, None, None]
         return np.where(tag == 0, H_int, np.where(tag == 1, H_wall, H_far)) * ln[..., None]
+
+    # ------------------------------------------------------------------ period grid
+    def set_period_steps(self, Nt):
+        """Equal DIRK steps of dt = T / Nt from t = 0: the stage times at which gbar is
+        tabulated (gbar(0) = g_h at t = 0, the map's own Jacobian)."""
+        from . import dirk
+        self.Nt_grid = Nt
+        self._tab = dirk.tableau()
+        self._gcache = {}
+
+    def gbar_at(self, mu, t):
+        """gbar at a stage time of the period grid (or the frozen pose for t = None).  The
+        table is built once per mu by the DIRK of the GCL; complex mu is allowed, so that
+        complex-step derivatives in mu include d gbar / d mu."""
+        if t is None:
+            return self.geometric_g(mu, None)
+        key = tuple(np.asarray(mu).ravel().tolist())
+        tab = self._gcache.get(key)
+        if tab is None:
+            A, b, c = self._tab
+            dt = self.T / self.Nt_grid
+            g = self.geometric_g(mu, 0.0)
+            tab = {round(0.0, 10): g}
+            for n in range(self.Nt_grid):
+                t0 = n * dt
+                stages, g = self.gbar_dirk(mu, t0, dt, g, self._tab)
+                for i in range(len(b)):
+                    tab[round(t0 + c[i] * dt, 10)] = stages[i]   # the sweeps' own stage times
+            self._gcache[key] = tab
+        k = round(float(np.real(t)), 10)
+        if k not in tab:
+            raise KeyError(f"t = {t} is not a stage time of the period grid")
+        return tab[k]
+
+    # ------------------------------------------------------------------ DG interface
+    def residual_local(self, uS, uN, mu, t):
+        """The base-class interface (used by residual, block Jacobians, dr/dmu and the
+        sweeps): the blended residual with gbar from the period grid."""
+        return self.residual_blended_local(uS, uN, mu, t, self.gbar_at(mu, t))
+
+    def qoi_rate(self, u, mu, t):
+        """Power and x-force on the airfoil from the wall numerical flux (per unit physical
+        length: the reference flux carries the factor |C^T N|)."""
+        us = np.asarray(u).reshape(np.shape(u)[:-1] + (self.Ne, 4, self.Np))
+        uN = us[..., self.nbr_safe, :, :]
+        gbar = self.gbar_at(mu, t)
+        xn, vn = self.nodal_map(mu, t)
+        Pw, Fx = 0.0, 0.0
+        for f in range(3):
+            H = self.face_flux_blended(us, uN, gbar, gbar[self.nbr_safe], f, xn, vn)
+            vf = self._geom(xn, vn, self.phi_f[f], self.dphi_f[f])[4]
+            wall = (self.tag[:, f] == 1).astype(np.float64)
+            wl = self.w_f[None, :] * (self.L[:, f] * wall)[:, None]
+            force = H[..., 1:3]
+            Pw = Pw + np.einsum("eq,...eq->...", wl, force[..., 0] * vf[..., 0] + force[..., 1] * vf[..., 1])
+            Fx = Fx + np.einsum("eq,...eq->...", wl, force[..., 0])
+        return Pw, Fx
+
+    def dqoi_du(self, u, mu, t):
+        """d(P^h, F_x^h)/du [2, Nu] (face-local to wall elements: one complex perturbation
+        of local dof (a, i) in every element at once is exact)."""
+        nb, Ne, Np = self.nb, self.Ne, self.Np
+        us = np.asarray(u, dtype=np.float64).reshape(Ne, 4, Np)
+        gbar = self.gbar_at(mu, t)
+        xn, vn = self.nodal_map(mu, t)
+        E = np.eye(nb).reshape(nb, 1, 4, Np)
+        uS = us[None] + 1j * CS_STEP * E
+        uN = us[self.nbr_safe][None] + 0j
+        out = np.zeros((2, Ne, nb))
+        for f in range(3):
+            H = self.face_flux_blended(uS, uN, gbar, gbar[self.nbr_safe], f, xn, vn)
+            vf = self._geom(xn, vn, self.phi_f[f], self.dphi_f[f])[4]
+            wall = (self.tag[:, f] == 1).astype(np.float64)
+            wl = self.w_f[None, :] * (self.L[:, f] * wall)[:, None]
+            force = H[..., 1:3]
+            pw = np.einsum("eq,deq->de", wl, force[..., 0] * vf[..., 0] + force[..., 1] * vf[..., 1])
+            fx = np.einsum("eq,deq->de", wl, force[..., 0])
+            out[0] += np.imag(pw).T / CS_STEP
+            out[1] += np.imag(fx).T / CS_STEP
+        return out.reshape(2, self.Nu)
 
     def gbar_dirk(self, mu, t0, dt, g0, tableau):
         """gbar at the stages and at the end of one DIRK step from gbar(t0) = g0: the GCL

@@ -140,3 +140,110 @@ def test_complex_step_derivative_matches_central_differences():
     h = 1e-6
     fd = (dg.residual_blended(u + h * d, MU_C0, 0.8, gbar) - dg.residual_blended(u - h * d, MU_C0, 0.8, gbar)) / (2 * h)
     assert np.max(np.abs(cs - fd)) <= 1e-6 * np.max(np.abs(cs))
+
+
+# ---------------------------------------------------------------------------- sweeps
+from oracle import periodic as P  # noqa: E402
+
+
+def test_rigid_limit_sweep_is_the_rigid_sweep():
+    mesh = config_mesh("tiny")
+    rig = DG(mesh, 1)
+    bl = BlendedDG(mesh, 1, r1=1e6, r2=2e6)
+    bl.set_period_steps(4)
+    u0 = _u(rig, 21).reshape(-1)
+    a = P.primal_sweep(rig, MU_C0, u0, 4, store=False)
+    b = P.primal_sweep(bl, MU_C0, u0, 4, store=False)
+    assert np.max(np.abs(b.u[-1] - a.u[-1])) <= 1e-11 * np.max(np.abs(a.u[-1]))
+    assert abs(b.W - a.W) <= 1e-11 * abs(a.W) and abs(b.Jx - a.Jx) <= 1e-11 * abs(a.Jx)
+
+
+def test_uniform_flow_survives_a_period_with_the_gcl_only():
+    class NoGCL(BlendedDG):
+        def gbar_at(self, mu, t):                # the map's own g_h instead of the GCL field
+            return self.geometric_g(mu, t)
+
+    mesh = box(5, 5, seed=2, **BIG)
+    for cls, uniform in ((BlendedDG, True), (NoGCL, False)):
+        dg = cls(mesh, 1)
+        dg.set_period_steps(10)
+        g0 = dg.geometric_g(MU_C0, 0.0)
+        u0 = (g0[:, None, :] * dg.Uinf[None, :, None]).reshape(-1)
+        tr = P.primal_sweep(dg, MU_C0, u0, 10, store=False, newton_tol=1e-14)
+        U = tr.u[-1].reshape(dg.Ne, 4, dg.Np) / dg.gbar_at(MU_C0, dg.T)[:, None, :]
+        dev = np.max(np.abs(U - dg.Uinf[None, :, None]))
+        if uniform:
+            assert dev < 1e-10
+        else:
+            assert dev > 1e-8
+
+
+@pytest.fixture(scope="module")
+def blended_tiny():
+    dg = BlendedDG(config_mesh("tiny"), 1)     # far field at r = 10: the blend zone is inside
+    dg.set_period_steps(4)
+    u0 = _u(dg, 23).reshape(-1)
+    tr = P.primal_sweep(dg, MU_C0, u0, 4)
+    return dg, tr
+
+
+def test_blended_tangent_sweep_matches_finite_differences(blended_tiny):
+    dg, tr = blended_tiny
+    v = np.random.default_rng(2).standard_normal(dg.Nu)
+    eps = 1e-6
+    up = P.primal_sweep(dg, MU_C0, tr.u[0] + eps * v, 4, store=False, newton_tol=1e-14).u[-1]
+    um = P.primal_sweep(dg, MU_C0, tr.u[0] - eps * v, 4, store=False, newton_tol=1e-14).u[-1]
+    fd = (up - um) / (2 * eps)
+    tv = P.tangent_sweep(dg, tr, v)
+    assert np.max(np.abs(tv - fd)) <= 1e-6 * np.max(np.abs(fd))
+
+
+def test_blended_duality(blended_tiny):
+    dg, tr = blended_tiny
+    rng = np.random.default_rng(3)
+    v, w = rng.standard_normal(dg.Nu), rng.standard_normal(dg.Nu)
+    lhs = w @ P.tangent_sweep(dg, tr, v)
+    lam0, _ = P.adjoint_sweep(dg, tr, w)
+    assert abs(lhs - lam0 @ v) <= 1e-11 * abs(lhs)
+
+
+def test_dr_dmu_includes_the_gcl_history():
+    """Complex step in mu runs through the tabulated gbar (its DIRK history depends on
+    mu), and matches central differences of the residual with gbar rebuilt per mu."""
+    dg = BlendedDG(box(4, 4, seed=5, **BIG), 1)
+    dg.set_period_steps(6)
+    A, b, c = dirk.tableau()
+    t = 3 * dg.T / 6 + c[1] * dg.T / 6
+    u = (dg.geometric_g(MU_C0, t)[:, None, :] * dg.Uinf[None, :, None]
+         + state_perturbation(dg.Ne, 1, seed=8, amp=3e-2).reshape(dg.Ne, 4, dg.Np)).reshape(-1)
+    cs = dg.dr_dmu(u, MU_C0, t)
+    h = 1e-6
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        fd = (dg.residual(u, MU_C0 + e, t) - dg.residual(u, MU_C0 - e, t)) / (2 * h)
+        assert np.max(np.abs(cs[:, j] - fd)) <= 1e-6 * max(np.max(np.abs(fd)), 1e-8)
+
+
+def test_blended_periodic_gradient_matches_finite_differences():
+    """Shooting and the periodic adjoint run unchanged on the blended residual; the
+    gradient (through dr/dmu, which carries d gbar / d mu) matches central differences
+    of re-shot periodic QoIs."""
+    nt = 4
+    dg = BlendedDG(config_mesh("tiny"), 1)
+    dg.set_period_steps(nt)
+    u0 = (dg.geometric_g(MU_C0, 0.0)[:, None, :] * dg.Uinf[None, :, None]).reshape(-1)
+    u0p, tr, _ = P.shoot_nk(dg, MU_C0, u0, nt, tol=1e-12)
+    w = np.array([1.0, 0.5])
+    F, grad, _ = P.periodic_gradient(dg, tr, w, tol=1e-13)
+    tau = 1e-4
+    fd = np.zeros(3)
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = tau
+        vals = []
+        for sgn in (1, -1):
+            _, trj, _ = P.shoot_nk(dg, MU_C0 + sgn * e, u0p, nt, tol=1e-12)
+            vals.append(w[0] * trj.W + w[1] * trj.Jx)
+        fd[j] = (vals[0] - vals[1]) / (2 * tau)
+    assert np.linalg.norm(grad - fd) <= 1e-6 * np.linalg.norm(fd)
