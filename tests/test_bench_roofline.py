@@ -40,3 +40,9 @@ def test_folded_fp32_operator_bytes():
     assert abs(r["achieved"] - 2048 * (3 * nb * nb + 5 * nb) * 4 / 10e-6 / 1e9) < 1e-6
     assert abs(r["frac"] - r["achieved"] / 6700.0) < 1e-12
     assert r["traffic"] is None                      # no capture of this class on file
+
+
+def test_l2_note_flags_small_working_sets():
+    from pp_inputs import CONFIGS
+    assert "far larger than L2" in bench.l2_note(dict(ne=2048, Nt=100), CONFIGS["c1"], "fp64")
+    assert "not a bench value" in bench.l2_note(dict(ne=64, Nt=20), CONFIGS["c0"], "fp64")
