@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--profile-step", type=int, default=0, metavar="NT",
+                    help="profiler capture mode: one primal + adjoint sweep over NT steps of the workload's "
+                         "step size (period and motion amplitudes scaled by NT / Nt), no timing, no bench line")
     return ap.parse_args()
 
 
@@ -262,7 +265,8 @@ def run_ours(args, rank, world, local_rank):
 
 
 def roofline_for(kernel, res, peaks, fp64_tflops, c):
-    """Algorithmic work per launch of the timed kernel class (counts in the design doc)."""
+    """Algorithmic work per launch of the timed kernel class: FLOPs or bytes per element of
+    the kernel's definition times the elements one launch processes."""
     p = c["p"]
     Np = (p + 1) * (p + 2) // 2
     nb = 4 * Np
@@ -310,8 +314,44 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c):
     return None
 
 
+def profile_step(args):
+    """One primal sweep plus one adjoint sweep (F = J_E, dF/dmu) over args.profile_step steps
+    of the workload's step size, from the free stream, for profiler captures.  A shorter
+    period keeps the time step: T and the motion amplitudes are scaled by NT / Nt, so the
+    capture runs the same kernels while holding a few GB of device memory."""
+    import numpy as np
+    import torch
+
+    from paper_1512_00616_gb300 import api as A
+    from pp_inputs import CONFIGS, PHYS, config_mesh, config_mu, free_stream_state
+    c = CONFIGS[args.config]
+    Nt = args.profile_step
+    mesh = config_mesh(args.config)
+    mu = config_mu(args.config)
+    T = PHYS["T"] * Nt / c["Nt"]
+    if Nt < c["Nt"]:
+        mu = mu * (T / PHYS["T"])
+    cfg = A.pp_config_default(p=c["p"], kin=c["kin"], T=T,
+                              precision=A.PP_PREC_MIXED if args.precision == "mixed" else A.PP_PREC_FP64)
+    ctx = A.pp_create(cfg)
+    m = A.pp_mesh_create(ctx, mesh.verts, mesh.tris, mesh.ftag)
+    ne, _, nu = A.pp_mesh_info(m)
+    u0 = torch.tensor(free_stream_state(ne, c["p"]).reshape(-1), dtype=torch.float64, device="cuda")
+    uN, lamN, lam0 = torch.zeros_like(u0), torch.zeros_like(u0), torch.zeros_like(u0)
+    torch.cuda.synchronize()
+    A.pp_primal_period(ctx, m, mu, u0, Nt, u_final=uN)
+    A.pp_adjoint_sweep(ctx, lamN, lam0, weights=np.array([-1.0 / T, 0.0]), n_mu=len(mu))
+    torch.cuda.synchronize()
+    print("profile step ok", float(uN.norm()), float(lam0.norm()), A.pp_sweep_counts(ctx))
+    A.pp_mesh_destroy(m)
+    A.pp_destroy(ctx)
+
+
 def main():
     args = parse()
+    if args.profile_step > 0:
+        profile_step(args)
+        return
     if args.roofline_kernel is None:
         args.roofline_kernel = "stage_op32" if args.precision == "mixed" else "stage_op"
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -108,7 +108,9 @@ void pp_config_default(pp_config* cfg);
    operator with the block-Jacobi preconditioner folded in (normal and transposed)
    and transposed Jacobian copies.  About 420 MB per stage for 2048 elements at p = 3
    in FP64; with checkpoint_stride K only one K-step segment of stages is kept.
-   Errors: PP_EINVAL (p out of range, null pointers), PP_ECUDA. */
+   One process uses one CUDA device: every context of the process must name the same
+   cfg->device (the kernels' launch set-up is cached per process).
+   Errors: PP_EINVAL (p out of range, null pointers, a second device), PP_ECUDA. */
 int pp_create(const pp_config* cfg, pp_ctx** out);
 int pp_destroy(pp_ctx* ctx);
 const char* pp_last_error(const pp_ctx* ctx);
@@ -153,8 +155,11 @@ int pp_qoi_rate(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, do
      kept until the process exits.  Meshes of more than 65536 elements are rejected with
      PP_EINVAL.
    - First call: the first call on a device looks up the array's device address
-     (cudaGetSymbolAddress) with that device current.  Make this first call before any
-     stream capture.
+     (cudaGetSymbolAddress) with that device current, under a lock, and caches it for the
+     life of the process.  Make this first call before any stream capture.  A
+     cudaDeviceReset of the device invalidates the cached address (as it invalidates every
+     context of this library on that device): do not call this function on that device
+     after a reset.
    - Concurrency: every call shares the one array.  Calls that overlap on the GPU, e.g.
      on different streams or from different contexts on the same device, race.  The
      finishing counter is cleared at the start of each call; other contents are

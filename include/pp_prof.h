@@ -45,6 +45,21 @@ struct pp_ctx;
 int pp_sweep_counts(const struct pp_ctx* ctx, int64_t* newton, int64_t* gmres_primal, int64_t* gmres_tangent,
                     int64_t* gmres_adjoint);
 
+/* Applies one operator of the stored linearization of DIRK step `step` (0 .. Nt-1), stage
+   `stage` (0 .. 2) to x, for tests of the stored blocks against dense products of the same
+   matrices (c = a_ii dt, D = block diagonal of M - c J; the operators of Eqs.
+   dirk-sens-mvp and uns-disc-adj-dirk2):
+     kind 0: y = (M - c J) x                       trans 1: y = (M - c J)^T x
+     kind 1: y = D^{-1} x (block-Jacobi inverse)   trans 1: y = D^{-T} x
+     kind 2: y = (M - c J) D^{-1} x (the folded operator I + B)
+                                                   trans 1: y = (M - c J)^T D^{-T} x
+   prec 0 uses the FP64 data, prec 1 the FP32 copies of PP_PREC_MIXED (x, y cast through
+   FP32).  x, y: DEVICE FP64 [N_u], distinct.  With a checkpointed linearization the
+   step's segment is recomputed first.  Errors: PP_ESTATE (no sweep stored, or the
+   requested data is not stored in this mode), PP_EINVAL. */
+int pp_stage_apply(struct pp_ctx* ctx, int step, int stage, int kind, int trans, int prec, const double* x,
+                   double* y);
+
 /* Measures the device's FP64 FMA throughput (TFLOP/s, 2 flops per FMA) with an
    unrolled dependent-chain kernel over all SMs; returns PP_OK or PP_ECUDA. */
 int pp_measure_fp64_peak(int device, double* tflops);

@@ -27,6 +27,7 @@ EXPORTED = [
     "pp_steady_state",
     # include/pp_prof.h
     "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
+    "pp_stage_apply",
     # include/pp_learn.h
     "pp_gemm_f32", "pp_gemm_f64", "pp_bias_act_f32", "pp_gelu_backward_f32", "pp_colsum_f32", "pp_mse_f32",
     "pp_adam_f32", "pp_syevj_f64",
@@ -92,6 +93,7 @@ def _load():
         "pp_prof_counts": (I, [C.POINTER(C.c_int64)]),
         "pp_measure_fp64_peak": (I, [I, dp]),
         "pp_sweep_counts": (I, [P] + [C.POINTER(C.c_int64)] * 4),
+        "pp_stage_apply": (I, [P, I, I, I, I, I, P, P]),
         "pp_gemm_f32": (I, [I, I, I, C.c_float, P, I, I, P, I, I, C.c_float, P, I, P]),
         "pp_gemm_f64": (I, [I, I, I, D, P, I, I, P, I, I, D, P, I, P]),
         "pp_bias_act_f32": (I, [I, I, P, P, P, I, P]),
@@ -298,6 +300,12 @@ def pp_sweep_counts(ctx):
     v = [C.c_int64() for _ in range(4)]
     _check(ctx, _lib.pp_sweep_counts(ctx, *[C.byref(x) for x in v]))
     return dict(newton=v[0].value, gmres_primal=v[1].value, gmres_tangent=v[2].value, gmres_adjoint=v[3].value)
+
+
+def pp_stage_apply(ctx, step, stage, kind, x, y, trans=False, prec=0):
+    """y = one stored stage operator applied to x (kind 0: M - cJ, 1: D^-1, 2: (M - cJ) D^-1)."""
+    _check(ctx, _lib.pp_stage_apply(ctx, int(step), int(stage), int(kind), int(bool(trans)), int(prec),
+                                    _dev(x, "x"), _dev(y, "y")))
 
 
 # --------------------------------------------------------------------------- learned warm start (include/pp_learn.h)

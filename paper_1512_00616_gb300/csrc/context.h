@@ -144,6 +144,7 @@ int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const
              double tol, double* u0_out, double* qoi, pp_shoot_stats* stats);
 int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
                      const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats);
+int stage_apply(pp_ctx* ctx, int step, int i, int kind, int trans, int prec, const double* x, double* y);
 }  // namespace pp
 
 #define PP_CK(...)                                                                                   \

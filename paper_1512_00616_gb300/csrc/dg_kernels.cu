@@ -10,6 +10,8 @@
 //
 // Layouts: u[e][a][i] (nb = 4 Np doubles per element, contiguous); Jacobian
 // blocks [e][slot][col][row] (column-major nb x nb).
+#include <mutex>
+
 #include "flux.cuh"
 #include "prof.h"
 #include "../../include/pp_prof.h"
@@ -588,11 +590,17 @@ cudaError_t launch_jacobian(const DevMesh& m, const DevTables& tb, const Phys& p
                             const double* u, double* J, cudaStream_t st) {
   ProfScope ps(PP_K_JACOBIAN, st);
   const size_t bytes = sizeof(double) * JacSmem(tb.nb, tb.Np, tb.nqv).total;
-  static size_t configured = 0;
-  if (bytes > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = bytes;
+  {
+    // largest dynamic shared memory requested so far (contexts of several degrees may share
+    // the process; one device per process, see pp_create)
+    static std::mutex mu;
+    static size_t configured = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (bytes > configured) {
+      cudaError_t e = cudaFuncSetAttribute(k_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+      configured = bytes;
+    }
   }
   k_jacobian<<<m.ne, JAC_THREADS, bytes, st>>>(m, tb, ph, fr, u, J);
   return cudaGetLastError();

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <utility>
 
@@ -426,6 +427,13 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       (cfg->precision == PP_PREC_MIXED && (cfg->inner_maxit < 1 || cfg->inner_maxit > 60)) ||
       cfg->checkpoint_stride < 0)
     return PP_EINVAL;
+  {
+    // the launch set-up cached by the kernels' host wrappers is per process: one device
+    static std::atomic<int> process_device{-1};
+    int expected = -1;
+    if (!process_device.compare_exchange_strong(expected, cfg->device) && expected != cfg->device)
+      return PP_EINVAL;
+  }
   pp_ctx* ctx = new pp_ctx();
   ctx->cfg = *cfg;
   ctx->device = cfg->device;
@@ -765,6 +773,12 @@ int pp_periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int 
   PP_TRY(check_mu(ctx, n_mu));
   PP_CK(cudaSetDevice(ctx->device));
   return periodic_adjoint(ctx, mesh, mu, n_mu, u0, Nt, weights, F, dFdmu, lam_Nt, stats);
+}
+
+int pp_stage_apply(pp_ctx* ctx, int step, int stage, int kind, int trans, int prec, const double* x, double* y) {
+  if (!ctx) return PP_EINVAL;
+  PP_CK(cudaSetDevice(ctx->device));
+  return stage_apply(ctx, step, stage, kind, trans, prec, x, y);
 }
 
 }  // extern "C"

@@ -905,13 +905,9 @@ cudaError_t launch_fold_blocks(const DevMesh& m, int nb, const S* J, const S* Ai
   const size_t smem = sizeof(S) * 2 * nb * nb;
 #define PP_FOLD(NBV)                                                                                     \
   case NBV: {                                                                                            \
-    static bool attr = false;                                                                            \
-    if (!attr) {                                                                                         \
-      cudaError_t e = cudaFuncSetAttribute(k_fold_blocks<NBV, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                           (int)smem);                                                  \
-      if (e != cudaSuccess) return e;                                                                    \
-      attr = true;                                                                                       \
-    }                                                                                                    \
+    static const cudaError_t attr =                                                                      \
+        cudaFuncSetAttribute(k_fold_blocks<NBV, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (attr != cudaSuccess) return attr;                                                                \
     k_fold_blocks<NBV, S><<<m.ne * 3, 256, smem, st>>>(m, J, Ainv, c, BN, BT);                           \
     break;                                                                                               \
   }
@@ -972,13 +968,12 @@ cudaError_t launch_gmres_backsolve(int ncols, int m, const double* H, const doub
 
 // One CTA per SM at most (fewer for short vectors).
 int cgs_blocks(int64_t n) {
-  static int cap = 0;
-  if (cap == 0) {
+  static const int cap = [] {  // thread-safe static initialization; one device per process
     int dev = 0, sms = CGS_MAX_BLOCKS;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cap = sms < CGS_MAX_BLOCKS ? sms : CGS_MAX_BLOCKS;
-    if (cap < 1) cap = 1;
-  }
+    int c = sms < CGS_MAX_BLOCKS ? sms : CGS_MAX_BLOCKS;
+    return c < 1 ? 1 : c;
+  }();
   int64_t b = (n + CGS_T - 1) / CGS_T;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);

@@ -4,6 +4,8 @@
 // not call cudaMalloc can use it.  Example callers: code running under a memory pool or
 // allocator that forbids outside allocations, or code that must not allocate after
 // start-up.
+#include <mutex>
+
 #include "context.h"
 #include "../../include/pp.h"
 
@@ -19,10 +21,13 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
 
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mutex;  // first lookups from several host threads do not race
 
-// Device address of the scratch array on `device` (which must be current); looked up once.
+// Device address of the scratch array on `device` (which must be current); looked up once
+// per device.  A cudaDeviceReset of that device makes the cached address stale.
 int scratch_address(pp_ctx* ctx, int device, double** out) {
   if (device < 0 || device >= kMaxDevices) return set_error(ctx, PP_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_ptr[device]) {
     double* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);

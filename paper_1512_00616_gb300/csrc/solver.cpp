@@ -877,4 +877,57 @@ int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_m
   return PP_OK;
 }
 
+// --------------------------------------------------------------------------- stored operators
+// Applies one operator of the stored linearization of step `step`, stage i (diagnostics):
+//   kind 0: y = (M - c J) x,           trans: (M - c J)^T x
+//   kind 1: y = D^{-1} x,              trans: D^{-T} x     (D = block diagonal of M - c J)
+//   kind 2: y = (I + B) x = (M - c J) D^{-1} x,  trans: (M - c J)^T D^{-T} x
+// with c = a_ii dt.  prec 1 applies the FP32 copies of the mixed-precision mode (x and y are
+// cast through FP32 work vectors).  x, y: DEVICE FP64 [N_u], distinct.
+int stage_apply(pp_ctx* ctx, int step, int i, int kind, int trans, int prec, const double* x, double* y) {
+  if (!ctx->lin_valid || !ctx->lin_mesh) return set_error(ctx, PP_ESTATE, "pp_stage_apply: no stored linearization");
+  if (step < 0 || step >= ctx->lin_Nt || i < 0 || i > 2 || kind < 0 || kind > 2 || trans < 0 || trans > 1 ||
+      prec < 0 || prec > 1 || !x || !y || x == y)
+    return set_error(ctx, PP_EINVAL, "pp_stage_apply: bad arguments");
+  if (prec == 1 && ctx->cfg.precision != PP_PREC_MIXED)
+    return set_error(ctx, PP_EINVAL, "pp_stage_apply: FP32 copies exist in PP_PREC_MIXED only");
+  PP_TRY(ensure_segment(ctx, step));
+  const pp_mesh* mesh = ctx->lin_mesh;
+  const DevMesh& m = mesh->dev;
+  const int64_t n = ctx->ws_nu;
+  const int nb = ctx->tb.nb;
+  StageView sv = stored_stage(ctx, step, i);
+  if (prec == 0) {
+    if (kind == 0) {
+      if (trans && sv.JT) PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.JT, 1.0, -sv.c, x, y, 0, ctx->stream));
+      else PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.J, 1.0, -sv.c, x, y, trans, ctx->stream));
+    } else if (kind == 1) {
+      if (!sv.Ainv) return set_error(ctx, PP_ESTATE, "pp_stage_apply: no FP64 block inverse stored");
+      if (trans && sv.AinvT) PP_CK(launch_block_apply<double>(m, nb, sv.AinvT, x, y, 0, ctx->stream));
+      else PP_CK(launch_block_apply<double>(m, nb, sv.Ainv, x, y, trans, ctx->stream));
+    } else {
+      const double* Bf = trans ? sv.BT : sv.BN;
+      if (!Bf) return set_error(ctx, PP_ESTATE, "pp_stage_apply: no FP64 folded operator stored");
+      PP_CK(launch_stream_rows<double>(m, ctx->tb, nb, 3, Bf, 0.0, 1.0, x, y, ctx->stream));
+    }
+  } else {
+    if (!sv.J32) return set_error(ctx, PP_ESTATE, "pp_stage_apply: no FP32 copies stored");
+    float* x32 = ctx->d_vec32 + 2 * n;
+    float* y32 = ctx->d_vec32 + 3 * n;
+    PP_CK(launch_cast<double, float>(n, x32, x, ctx->stream));
+    if (kind == 0) {
+      PP_CK(launch_stage_matvec<float>(m, ctx->tb, trans ? sv.JT32 : sv.J32, 1.0, -sv.c, x32, y32, 0, ctx->stream));
+    } else if (kind == 1) {
+      PP_CK(launch_block_apply<float>(m, nb, trans ? sv.AT32 : sv.A32, x32, y32, 0, ctx->stream));
+    } else {
+      const float* Bf = trans ? sv.BT32 : sv.BN32;
+      if (!Bf) return set_error(ctx, PP_ESTATE, "pp_stage_apply: no FP32 folded operator stored");
+      PP_CK(launch_stream_rows<float>(m, ctx->tb, nb, 3, Bf, 0.0, 1.0, x32, y32, ctx->stream));
+    }
+    PP_CK(launch_cast<float, double>(n, y, y32, ctx->stream));
+  }
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  return check_stream_kernels(ctx);
+}
+
 }  // namespace pp

@@ -262,19 +262,27 @@ template <int NB, int NBLK, class S>
 cudaError_t launch_rows(const DevMesh& m, const DevTables& tb, const S* B, double alpha, double beta, const S* x,
                         S* y, cudaStream_t st) {
   using Sh = StreamShape<NB, NBLK, S>;
-  static int grid = 0;  // resident CTAs per SM x SM count (same device for the process)
-  if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_stream_rows<NB, NBLK, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Sh::SMEM);
-    if (e != cudaSuccess) return e;
+  // resident CTAs per SM x SM count, set up once per process (thread-safe static
+  // initialization; libpp serves one device per process, see pp_create)
+  struct Setup {
+    cudaError_t err;
+    int grid;
+  };
+  static const Setup setup = [] {
+    Setup r{cudaSuccess, 0};
+    r.err = cudaFuncSetAttribute(k_stream_rows<NB, NBLK, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+    if (r.err != cudaSuccess) return r;
     int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_rows<NB, NBLK, S>, Sh::THREADS, Sh::SMEM);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    grid = per_sm * sms;
-  }
+    r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_rows<NB, NBLK, S>, Sh::THREADS, Sh::SMEM);
+    if (r.err != cudaSuccess) return r;
+    if ((r.err = cudaGetDevice(&dev)) != cudaSuccess) return r;
+    if ((r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+    if (per_sm < 1) r.err = cudaErrorInvalidConfiguration;
+    r.grid = per_sm * sms;
+    return r;
+  }();
+  if (setup.err != cudaSuccess) return setup.err;
+  const int grid = setup.grid;
   const int g = m.ne < grid ? m.ne : grid;
   if (g < 1) return cudaSuccess;
   k_stream_rows<NB, NBLK, S><<<g, Sh::THREADS, Sh::SMEM, st>>>(m, tb, B, alpha, beta, x, y);
