@@ -13,14 +13,26 @@ readings the paper leaves open (it defers spatial details to other papers):
   physical gradients are grad_x = Q grad_X, physical normals n = Q N;
 * inviscid interface flux: Roe's flux of F(U).n - (v_G.n) U with Harten's
   entropy fix (delta = 0.1 c);
-* viscous interface flux: interior penalty, {F_vis}.n + sigma (U+ - U-) with
-  sigma = 2 mu_visc (p+1)^2 |f| / min(|K-|, |K+|) (compact: element plus its
-  face neighbours);
-* wall (no-slip, adiabatic): ghost U_b = (rho-, rho- v_G, rho-(e- + |v_G|^2/2)),
-  exact ALE wall flux F(U_b).n - (v_G.n) U_b, viscous flux from U_b and the
-  interior gradient with zero normal heat flux;
-* far field: Roe flux against the free stream, interior viscous flux, penalty
-  towards the free stream;
+* viscous terms: the compact discontinuous Galerkin (CDG) scheme the paper
+  names in Sec. 6, written from Peraire and Persson's definition.  With U_hat
+  the face value of U (the other side's trace on an interior face, the boundary
+  state on a boundary face), the lifting of face f into element K is the
+  degree-p field r_f with  int_K r_f . tau = int_f (U_hat - U_K) tau . n_K  for
+  all tau; on straight faces r_f = n_f s_f l_f with s_f = |f| / (2 |K|) and l_f
+  the scalar lifting of the jump on the reference element.  Volume term:
+  F_vis(U, grad U + sum_f r_f) over the faces K lifts.  Face flux: on an
+  interior face the element with the smaller index supplies the viscous flux
+  F_vis(U_S, grad U_S + r_f^S) . n with the lifting of that face alone, and U_hat
+  is the other side's trace (the C12 switch of LDG, so the stencil is the
+  element and its face neighbours); on boundary faces the element itself lifts
+  the jump to the boundary state and a penalty C11 (U_b - U) with
+  C11 = 10 mu_visc |f| / (2 |K|) (10 mu / h) is added;
+* wall (no-slip, adiabatic): boundary state U_b = (rho-, rho- v_G,
+  rho-(e- + |v_G|^2/2)), exact ALE wall flux F(U_b).n - (v_G.n) U_b, viscous
+  flux F_vis(U_b, grad U + r_f) with zero heat flux;
+* far field: Roe flux against the free stream (or a prescribed boundary state,
+  for manufactured solutions), viscous flux F_vis(U, grad U + r_f) with the
+  lifting of the jump to that state;
 * force on the airfoil: the momentum components of the wall numerical flux
   (the momentum leaving the fluid through the wall), so that the power is
   P^h = int f . x' dS and the x-force F_x^h = int f . e1 dS (Eq. qoi).
@@ -39,7 +51,7 @@ from . import refelem
 KIN_HEAVE_PITCH = 0
 KIN_FOURIER6 = 1
 CS_STEP = 1e-30
-PENALTY_ETA = 2.0
+C11_ETA = 10.0   # boundary penalty C11 = C11_ETA mu_visc / h with h = 2 |K| / |f|
 
 
 def cabs(x):
@@ -85,7 +97,7 @@ def viscous_flux(U, dU, mu, Pr, gam, adiabatic=False):
     kq = 0.0 if adiabatic else mu / Pr * gam
     qx = -kq * de[..., 0]
     qy = -kq * de[..., 1]
-    zero = 0.0 * rho
+    zero = 0.0 * txx
     Fx = np.stack([zero, txx, txy, u * txx + v * txy - qx], -1)
     Fy = np.stack([zero, txy, tyy, u * txy + v * tyy - qy], -1)
     return np.stack([Fx, Fy], -1)
@@ -143,8 +155,12 @@ def dot_n(F, n):
 class DG:
     """The semi-discretization on a given mesh; see module docstring."""
 
-    def __init__(self, mesh, p, gamma=1.4, Pr=0.72, Mach=0.2, Re=1000.0, kin=KIN_HEAVE_PITCH, T=5.0):
+    def __init__(self, mesh, p, gamma=1.4, Pr=0.72, Mach=0.2, Re=1000.0, kin=KIN_HEAVE_PITCH, T=5.0,
+                 farfield=None):
+        """farfield: optional boundary state U_b(X) [..., 2] -> [..., 4] of the far-field faces
+        (default: the uniform free stream); used by manufactured-solution tests."""
         self.mesh = mesh
+        self.farfield = farfield
         self.p = p
         self.gam, self.Pr, self.Mach, self.Re = gamma, Pr, Mach, Re
         self.mu_visc = 1.0 / Re
@@ -217,27 +233,41 @@ class DG:
         nqf = len(self.s_f)
         self.phiN = np.zeros((Ne, 3, nqf, Np))
         self.dphiN = np.zeros((Ne, 3, nqf, Np, 2))
-        self.sigma = np.zeros((Ne, 3))
         for e in range(Ne):
             for f in range(3):
                 e2, g = self.nbr[e, f], self.nbr_face[e, f]
-                a_nb = self.area[e]
                 if e2 >= 0:
                     xi2 = refelem.face_points(g, 1.0 - self.s_f)
                     self.phiN[e, f] = self.basis.phi(xi2)
                     self.dphiN[e, f] = self.basis.dphi(xi2)
                     Xm = X0[e2] + xi2 @ B[e2].T
                     assert np.allclose(Xm, self.Xq_f[e, f], atol=1e-12)
-                    a_nb = self.area[e2]
                 else:  # boundary: placeholder values (the interior branch is masked out)
                     self.phiN[e, f] = self.phi_f[f]
                     self.dphiN[e, f] = self.dphi_f[f]
-                self.sigma[e, f] = PENALTY_ETA * self.mu_visc * (p + 1) ** 2 * self.L[e, f] / min(self.area[e], a_nb)
         self.nbr_safe = np.where(self.nbr >= 0, self.nbr, np.arange(Ne)[:, None])
         self.BinvT_nbr = self.BinvT[self.nbr_safe]                      # [Ne, 3, 2, 2]
 
         # mass matrix: M_e = detB * int phi_i phi_j over the reference triangle
         self.Mref = np.einsum("q,qi,qj->ij", self.w_v, self.phi_v, self.phi_v)
+
+        # CDG liftings.  The scalar lifting of a jump j given at the points of face f is
+        # l = sum_j phi_j (Mref^-1 c)_j with c_i = sum_q w_q phi_i(face point q) j_q, so that
+        # int_K r_f . tau = int_f j tau . n holds for r_f = n_f (|f| / detB) l (affine K).
+        # lift_v[f]: l at the volume points per unit jump at face point q; lift_f[f]: l at
+        # the points of face f itself.
+        Minv = np.linalg.inv(self.Mref)
+        self.lift_v = np.stack([self.phi_v @ Minv @ (self.phi_f[f].T * self.w_f[None, :]) for f in range(3)])
+        self.lift_f = np.stack([self.phi_f[f] @ Minv @ (self.phi_f[f].T * self.w_f[None, :]) for f in range(3)])
+        # the element that supplies the viscous flux of a face and lifts its jump: the
+        # element itself on boundary faces, the one with the smaller index on interior faces
+        self.flux_side = (self.nbr < 0) | (self.nbr > np.arange(Ne)[:, None])
+        self.s_own = self.L / self.detB[:, None]
+        self.s_nbr = self.L / self.detB[self.nbr_safe]
+        # the neighbour's lifting of its own face, in this element's point order (the face
+        # points are matched in reverse)
+        self.lift_fN = self.lift_f[np.where(self.nbr >= 0, self.nbr_face, 0)][:, :, ::-1, ::-1].copy()
+        self.c11 = np.where(self.nbr < 0, C11_ETA * self.mu_visc * self.L / self.detB[:, None], 0.0)
 
     # ------------------------------------------------------------------ kinematics
     def motion(self, mu, t):
@@ -274,9 +304,10 @@ class DG:
         return np.stack([vx, vy], -1)
 
     # ------------------------------------------------------------------ residual
-    def _face_flux(self, uS, uN, f, Q, Qd, hd, P):
-        """Numerical flux H (outward, per unit length) at the quadrature points of local face f."""
-        g = self.gam
+    def _traces(self, uS, uN, f, Q, Qd, hd, P):
+        """Both traces of U and their physical gradients at the points of local face f, the
+        physical outward normal, the mesh velocity and the face value U_hat of U (the
+        neighbour trace, the wall state or the far-field state by tag)."""
         Um = np.einsum("...eai,qi->...eqa", uS, self.phi_f[f])
         gm = np.einsum("edk,qik->eqid", P, self.dphi_f[f])
         dUm = np.einsum("...eai,eqid->...eqad", uS, gm)
@@ -287,28 +318,55 @@ class DG:
         n = np.einsum("dk,ek->ed", Q, self.N[:, f])[:, None, :]        # [Ne, 1, 2]
         vG = self.mesh_velocity(self.Xq_f[:, f], Qd, hd)                 # [Ne, nqf, 2]
         vn = vG[..., 0] * n[..., 0] + vG[..., 1] * n[..., 1]
-        sig = self.sigma[:, f][:, None, None]
-        mu, Pr = self.mu_visc, self.Pr
-
-        Fvm = viscous_flux(Um, dUm, mu, Pr, g)
-        # interior
-        Fvp = viscous_flux(Up, dUp, mu, Pr, g)
-        H_int = roe_flux(Um, Up, n, vn, g) - (0.5 * dot_n(Fvm + Fvp, n) + sig * (Up - Um))
-        # far field
-        Uinf = np.broadcast_to(self.Uinf, Um.shape) + 0.0 * Um
-        H_far = roe_flux(Um, Uinf, n, vn, g) - (dot_n(Fvm, n) + sig * (Uinf - Um))
-        # no-slip adiabatic wall
+        # no-slip wall state: interior density and internal energy, wall velocity
         rho = Um[..., 0]
         e_int = Um[..., 3] / rho - 0.5 * (Um[..., 1] ** 2 + Um[..., 2] ** 2) / rho**2
         vGb = vG + 0.0 * rho[..., None]
         Ub = np.stack([rho, rho * vGb[..., 0], rho * vGb[..., 1],
                        rho * (e_int + 0.5 * (vGb[..., 0] ** 2 + vGb[..., 1] ** 2))], -1)
-        Fvb = viscous_flux(Ub, dUm, mu, Pr, g, adiabatic=True)
-        H_wall = normal_flux(Ub, n, vn, g) - (dot_n(Fvb, n) + sig * (Ub - Um))
-
+        if self.farfield is None:
+            Uf = np.broadcast_to(self.Uinf, Um.shape) + 0.0 * Um
+        else:
+            Uf = np.broadcast_to(self.farfield(self.Xq_f[:, f]), Um.shape) + 0.0 * Um
         tag = self.tag[:, f][:, None, None]
-        H = np.where(tag == 0, H_int, np.where(tag == 1, H_wall, H_far))
+        Uhat = np.where(tag == 0, Up, np.where(tag == 1, Ub, Uf))
+        return Um, dUm, Up, dUp, n, vG, vn, Ub, Uf, Uhat
+
+    def _face_flux(self, uS, uN, f, Q, Qd, hd, P):
+        """Numerical flux H (outward, per unit length) at the quadrature points of local face f."""
+        g = self.gam
+        mu, Pr = self.mu_visc, self.Pr
+        Um, dUm, Up, dUp, n, vG, vn, Ub, Uf, Uhat = self._traces(uS, uN, f, Q, Qd, hd, P)
+        nf = n[:, 0, :]                                                  # [Ne, 2]
+        # lifted gradient of the side that supplies the viscous flux (this face's lifting only)
+        l_own = np.einsum("qp,...epa->...eqa", self.lift_f[f], Uhat - Um) * self.s_own[:, f][:, None, None]
+        Q_own = dUm + l_own[..., None] * nf[:, None, None, :]
+        l_nbr = np.einsum("eqp,...epa->...eqa", self.lift_fN[:, f], Up - Um) * self.s_nbr[:, f][:, None, None]
+        Q_nbr = dUp + l_nbr[..., None] * nf[:, None, None, :]
+        side = self.flux_side[:, f][:, None, None]
+        tag = self.tag[:, f][:, None, None]
+        US = np.where(side, np.where(tag == 1, Ub, Um), Up)
+        QS = np.where(side[..., None], Q_own, Q_nbr)
+        FvS_int = viscous_flux(US, QS, mu, Pr, g)
+        FvS_wall = viscous_flux(US, QS, mu, Pr, g, adiabatic=True)
+        FvS = np.where(tag[..., None] == 1, FvS_wall, FvS_int)
+        pen = self.c11[:, f][:, None, None] * (Uhat - Um)
+        inv_int = roe_flux(Um, Up, n, vn, g)
+        inv_far = roe_flux(Um, Uf, n, vn, g)
+        inv_wall = normal_flux(Ub, n, vn, g)
+        Hinv = np.where(tag == 0, inv_int, np.where(tag == 1, inv_wall, inv_far))
+        H = Hinv - (dot_n(FvS, n) + pen)
         return H, vG
+
+    def _volume_lifting(self, uS, uN, Q, Qd, hd, P):
+        """sum over the faces this element lifts of r_f at the volume points [.., Ne, nqv, 4, 2]."""
+        out = 0.0
+        for f in range(3):
+            Um, _, _, _, n, _, _, _, _, Uhat = self._traces(uS, uN, f, Q, Qd, hd, P)
+            w = (self.s_own[:, f] * self.flux_side[:, f])[:, None, None]
+            l = np.einsum("qp,...epa->...eqa", self.lift_v[f], Uhat - Um) * w
+            out = out + l[..., None] * n[:, 0, None, None, :]
+        return out
 
     def residual_local(self, uS, uN, mu, t):
         """r_e from the element's own state uS [..., Ne, 4, Np] and face-neighbour states
@@ -320,7 +378,7 @@ class DG:
         # volume term: int grad_x phi_i . (F_inv - U v_G - F_vis) dX
         U = np.einsum("...eai,qi->...eqa", uS, self.phi_v)
         gphys = np.einsum("edk,qik->eqid", P, self.dphi_v)
-        dU = np.einsum("...eai,eqid->...eqad", uS, gphys)
+        dU = np.einsum("...eai,eqid->...eqad", uS, gphys) + self._volume_lifting(uS, uN, Q, Qd, hd, P)
         vG = self.mesh_velocity(self.Xq_v, Qd, hd)
         Ftot = inviscid_flux(U, g) - U[..., None] * vG[..., None, :] \
             - viscous_flux(U, dU, self.mu_visc, self.Pr, g)
@@ -338,8 +396,8 @@ class DG:
         import copy
         sub = copy.copy(self)
         elems = np.asarray(elems)
-        for name in ("X0", "B", "detB", "area", "BinvT", "L", "N", "Xq_v", "Xq_f", "phiN", "dphiN", "sigma",
-                     "tag", "nbr", "nbr_face", "nbr_safe", "BinvT_nbr"):
+        for name in ("X0", "B", "detB", "area", "BinvT", "L", "N", "Xq_v", "Xq_f", "phiN", "dphiN", "flux_side",
+                     "s_own", "s_nbr", "lift_fN", "c11", "tag", "nbr", "nbr_face", "nbr_safe", "BinvT_nbr"):
             setattr(sub, name, getattr(self, name)[elems])
         sub.Ne = len(elems)
         sub.Nu = sub.Ne * 4 * self.Np

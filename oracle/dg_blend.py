@@ -19,8 +19,10 @@ the polynomial map, integrated exactly), r(gbar U_inf) = -U_inf D[C v_h] for any
 so a uniform flow stays uniform through every DIRK stage.  With b = 1 everywhere the
 residual is the rigid one (G = Q, g = 1, gbar = 1).
 
-Readings kept from the rigid oracle: fluxes, boundary states and the penalty (sigma on
-the reference face length), mass matrix of the reference element.
+Readings kept from the rigid oracle: fluxes, boundary states, the CDG viscous terms
+(liftings and the boundary penalty on the reference element and reference face length,
+where the elements are affine; the lifted reference gradient is mapped by G^-T of its
+side), mass matrix of the reference element.
 """
 import numpy as np
 
@@ -108,19 +110,11 @@ class BlendedDG(DG):
         xn, vn = self.nodal_map(mu, t)
         gN = gbar[self.nbr_safe]
 
-        def state(u, gb, phi, gradX):
-            UX = np.einsum("...eai,eqi->...eqa", u, phi)
-            gq = np.einsum("ei,eqi->eq", gb, phi)
-            dUX = np.einsum("...eai,eqid->...eqad", u, gradX)
-            dg = np.einsum("ei,eqid->eqd", gb, gradX)
-            U = UX / gq[..., None]
-            dU = (dUX - U[..., None] * dg[..., None, :]) / gq[..., None, None]   # grad_X U
-            return U, dU
-
         # volume
         G, g, C, GinvT, v, gradX = self._geom(xn, vn, self.phi_v, self.dphi_v)
         phi_e = np.broadcast_to(self.phi_v, (self.Ne,) + self.phi_v.shape)
-        U, dUX = state(uX, gbar, phi_e, gradX)
+        U, dUX = self._state(uX, gbar, phi_e, gradX)
+        dUX = dUX + self.volume_lifting_blended(uX, uN, gbar, gN, xn, vn)      # lifted grad_X U
         dU = np.einsum("eqik,...eqak->...eqai", GinvT, dUX)                    # grad_x U
         Ftot = inviscid_flux(U, gam) - U[..., None] * v[..., None, :] - viscous_flux(U, dU, mu_v, Pr, gam)
         FX = np.einsum("eqJi,...eqai->...eqaJ", C, Ftot)
@@ -132,53 +126,84 @@ class BlendedDG(DG):
             r = r - np.einsum("q,e,qj,...eqa->...eaj", self.w_f, self.L[:, f], self.phi_f[f], H)
         return r
 
-    def face_flux_blended(self, uX, uN, gbar, gN, f, xn, vn):
-        """Reference-face numerical flux |C^T N| H at the points of local face f
-        [.., Ne, nqf, 4] (outward from the element, per unit reference length)."""
-        gam, mu_v, Pr = self.gam, self.mu_visc, self.Pr
+    @staticmethod
+    def _state(u, gb, phi, gradX):
+        """U = U_X / gbar and its reference gradient grad_X U at points."""
+        UX = np.einsum("...eai,eqi->...eqa", u, phi)
+        gq = np.einsum("ei,eqi->eq", gb, phi)
+        dUX = np.einsum("...eai,eqid->...eqad", u, gradX)
+        dg = np.einsum("ei,eqid->eqd", gb, gradX)
+        U = UX / gq[..., None]
+        return U, (dUX - U[..., None] * dg[..., None, :]) / gq[..., None, None]
 
-        def state(u, gb, phi, gradX):
-            UX = np.einsum("...eai,eqi->...eqa", u, phi)
-            gq = np.einsum("ei,eqi->eq", gb, phi)
-            dUX = np.einsum("...eai,eqid->...eqad", u, gradX)
-            dg = np.einsum("ei,eqid->eqd", gb, gradX)
-            U = UX / gq[..., None]
-            return U, (dUX - U[..., None] * dg[..., None, :]) / gq[..., None, None]
-
+    def _traces_blended(self, uX, uN, gbar, gN, f, xn, vn):
+        """Both traces of U with their reference gradients at the points of local face f,
+        the geometry there (G^-T of both sides, C^T N, the physical normal n, v_h) and the
+        face value U_hat of U (neighbour trace, wall state or far-field state by tag)."""
         Gf, gf, Cf, GinvTf, vf, gradXf = self._geom(xn, vn, self.phi_f[f], self.dphi_f[f])
         phi_m = np.broadcast_to(self.phi_f[f], (self.Ne,) + self.phi_f[f].shape)
-        Um, dUXm = state(uX, gbar, phi_m, gradXf)
-        dUm = np.einsum("eqik,...eqak->...eqai", GinvTf, dUXm)
+        Um, dUXm = self._state(uX, gbar, phi_m, gradXf)
         # neighbour trace at the matched points, with the neighbour's own map (the
         # interpolated map is continuous across the face, its gradient is not)
         gradXn = np.einsum("ekl,eqjl->eqjk", self.BinvT_nbr[:, f], self.dphiN[:, f])
         nb = self.nbr_safe[:, f]
         GinvTp = self._geom_pts(xn[nb], vn[nb], self.phiN[:, f], gradXn)[3]
-        Up, dUXp = state(uN[..., f, :, :], gN[:, f], self.phiN[:, f], gradXn)
-        dUp = np.einsum("eqik,...eqak->...eqai", GinvTp, dUXp)
+        Up, dUXp = self._state(uN[..., f, :, :], gN[:, f], self.phiN[:, f], gradXn)
         nt = np.einsum("eqJi,eJ->eqi", Cf, self.N[:, f])                      # C^T N
         ln = np.sqrt(nt[..., 0] ** 2 + nt[..., 1] ** 2)
         n = nt / ln[..., None]
         vnrm = vf[..., 0] * n[..., 0] + vf[..., 1] * n[..., 1]
-        sig = self.sigma[:, f][:, None, None]
-        Fvm = viscous_flux(Um, dUm, mu_v, Pr, gam)
-        Fvp = viscous_flux(Up, dUp, mu_v, Pr, gam)
-
-        def dn(F):
-            return F[..., 0] * n[..., None, 0] + F[..., 1] * n[..., None, 1]
-
-        H_int = roe_flux(Um, Up, n, vnrm, gam) - (0.5 * dn(Fvm + Fvp) + sig * (Up - Um))
-        Uinf = np.broadcast_to(self.Uinf, Um.shape) + 0.0 * Um
-        H_far = roe_flux(Um, Uinf, n, vnrm, gam) - (dn(Fvm) + sig * (Uinf - Um))
         rho = Um[..., 0]
         e_int = Um[..., 3] / rho - 0.5 * (Um[..., 1] ** 2 + Um[..., 2] ** 2) / rho**2
         vb = vf + 0.0 * rho[..., None]
         Ub = np.stack([rho, rho * vb[..., 0], rho * vb[..., 1],
                        rho * (e_int + 0.5 * (vb[..., 0] ** 2 + vb[..., 1] ** 2))], -1)
-        H_wall = normal_flux(Ub, n, vnrm, gam) - (dn(viscous_flux(Ub, dUm, mu_v, Pr, gam, adiabatic=True))
-                                                   + sig * (Ub - Um))
+        Uinf = np.broadcast_to(self.Uinf, Um.shape) + 0.0 * Um
         tag = self.tag[:, f][:, None, None]
-        return np.where(tag == 0, H_int, np.where(tag == 1, H_wall, H_far)) * ln[..., None]
+        Uhat = np.where(tag == 0, Up, np.where(tag == 1, Ub, Uinf))
+        return dict(Um=Um, dUXm=dUXm, Up=Up, dUXp=dUXp, GinvTm=GinvTf, GinvTp=GinvTp, n=n, ln=ln, vf=vf,
+                    vn=vnrm, Ub=Ub, Uinf=Uinf, Uhat=Uhat)
+
+    def volume_lifting_blended(self, uX, uN, gbar, gN, xn, vn):
+        """sum over the faces this element lifts of the reference lifting N_f s_f l_f at the
+        volume points [.., Ne, nqv, 4, 2] (CDG in the reference coordinates, where the
+        elements are affine)."""
+        out = 0.0
+        for f in range(3):
+            tr = self._traces_blended(uX, uN, gbar, gN, f, xn, vn)
+            w = (self.s_own[:, f] * self.flux_side[:, f])[:, None, None]
+            l = np.einsum("qp,...epa->...eqa", self.lift_v[f], tr["Uhat"] - tr["Um"]) * w
+            out = out + l[..., None] * self.N[:, f][:, None, None, :]
+        return out
+
+    def face_flux_blended(self, uX, uN, gbar, gN, f, xn, vn):
+        """Reference-face numerical flux |C^T N| H at the points of local face f
+        [.., Ne, nqf, 4] (outward from the element, per unit reference length).  The CDG
+        viscous flux of the rigid oracle, with the liftings taken in the reference
+        coordinates and the lifted reference gradient mapped by G^-T of its side."""
+        gam, mu_v, Pr = self.gam, self.mu_visc, self.Pr
+        tr = self._traces_blended(uX, uN, gbar, gN, f, xn, vn)
+        Um, Up, Uhat, n, ln = tr["Um"], tr["Up"], tr["Uhat"], tr["n"], tr["ln"]
+        Nf = self.N[:, f][:, None, None, :]
+        l_own = np.einsum("qp,...epa->...eqa", self.lift_f[f], Uhat - Um) * self.s_own[:, f][:, None, None]
+        Q_own = np.einsum("eqik,...eqak->...eqai", tr["GinvTm"], tr["dUXm"] + l_own[..., None] * Nf)
+        l_nbr = np.einsum("eqp,...epa->...eqa", self.lift_fN[:, f], Up - Um) * self.s_nbr[:, f][:, None, None]
+        Q_nbr = np.einsum("eqik,...eqak->...eqai", tr["GinvTp"], tr["dUXp"] + l_nbr[..., None] * Nf)
+        side = self.flux_side[:, f][:, None, None]
+        tag = self.tag[:, f][:, None, None]
+        US = np.where(side, np.where(tag == 1, tr["Ub"], Um), Up)
+        QS = np.where(side[..., None], Q_own, Q_nbr)
+        FvS = np.where(tag[..., None] == 1, viscous_flux(US, QS, mu_v, Pr, gam, adiabatic=True),
+                       viscous_flux(US, QS, mu_v, Pr, gam))
+
+        def dn(F):
+            return F[..., 0] * n[..., None, 0] + F[..., 1] * n[..., None, 1]
+
+        pen = self.c11[:, f][:, None, None] * (Uhat - Um)
+        Hinv = np.where(tag == 0, roe_flux(Um, Up, n, tr["vn"], gam),
+                        np.where(tag == 1, normal_flux(tr["Ub"], n, tr["vn"], gam),
+                                 roe_flux(Um, tr["Uinf"], n, tr["vn"], gam)))
+        return (Hinv - (dn(FvS) + pen)) * ln[..., None]
 
     # ------------------------------------------------------------------ period grid
     def set_period_steps(self, Nt):
