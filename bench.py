@@ -28,8 +28,6 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) per launch of a kernel class on a workload, from one ncu
 # capture of the current kernel (profiles/ names the capture); absent -> null.
 MEASURED_TRAFFIC = {
-    # profiles/k_stream_rows_c1.md: dram__bytes_read.sum 77.70 MB + dram__bytes_write.sum 0.99 MB
-    ("stage_op", "c1"): 78.69e6,
 }
 
 METRIC = "DOF*stages/s fwd+adjoint"
@@ -43,11 +41,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c1")
-    ap.add_argument("--roofline-kernel", default=None,
-                    help="kernel class for the roofline (default: stage_op in fp64, stage_matvec32 in mixed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement (<= --steps)")
+    ap.add_argument("--oracle-stage", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--out", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-step", type=int, default=0, metavar="NT",
                     help="profiler capture mode: one primal + adjoint sweep over NT steps of the workload's "
@@ -101,42 +99,101 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle sample (CPU)
-def oracle_sample(config, budget_s):
-    """Times the oracle's element-local work of one stage-Newton iteration (residual and
-    exact complex-step Jacobian rows) on as many elements of the workload as fit in
-    budget_s, extrapolated linearly (the element loop is exactly linear) to the mesh.
-    The sparse LU factorization is NOT included, so the oracle's cost is understated."""
+def cpu_info():
+    """nproc and the CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return {"nproc": os.cpu_count(), "model": model or platform.processor() or platform.machine()}
+
+
+def oracle_stage(config, seed=1):
+    """The oracle's unit of stage work on the full workload, with its own code as it stands:
+    one stage-Newton iteration with a Jacobian refresh (the residual, the complex-step block
+    Jacobian, the SuperLU factorization of M - a_ii dt J and the solve; the calls
+    _stage_newton makes) and the matching adjoint stage (transposed solve, QoI derivatives,
+    dr/dmu and dq/dmu terms of the gradient; the calls adjoint_sweep makes).  Every primal
+    stage takes at least two such iterations (the first Newton iteration and the stored
+    linearization of the converged stage), so a stage costs at least 2 t_iter + t_adjoint:
+    DOF*stages/s = N_u / (2 t_iter + t_adjoint) is an upper bound on the oracle's speed."""
+    import resource
+
     import numpy as np
+    import scipy.sparse.linalg as spla
 
     from oracle.dg import DG
-    from pp_inputs import CONFIGS, config_mesh, config_mu, free_stream_state, state_perturbation
+    from oracle.dirk import tableau
+    from pp_inputs import CONFIGS, PHYS, config_mesh, config_mu, free_stream_state, state_perturbation
     c = CONFIGS[config]
     dg = DG(config_mesh(config), c["p"], kin=c["kin"])
     mu = config_mu(config)
-    u = (free_stream_state(dg.Ne, c["p"]) + state_perturbation(dg.Ne, c["p"], 1, amp=1e-3)).reshape(-1)
+    A, b, cc = tableau()
+    dt = PHYS["T"] / c["Nt"]
+    u = (free_stream_state(dg.Ne, c["p"]) + state_perturbation(dg.Ne, c["p"], seed, amp=1e-3)).reshape(-1)
+    M = dg.mass()
+    w = np.array([-1.0 / PHYS["T"], 0.0])           # F = J_E, as the GPU bench
+    lam = np.random.default_rng(seed).standard_normal(dg.Nu) * 1e-3
+    ti = cc[0] * dt
+    k = np.zeros_like(u)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
-    dg.residual(u, mu, 0.1)
-    t_res = time.perf_counter() - t0
-    done, t_jac, chunk = 0, 0.0, 32
-    while done < dg.Ne and t_jac < budget_s:
-        el = np.arange(done, min(done + chunk, dg.Ne))
-        t0 = time.perf_counter()
-        dg.jac_blocks_subset(u, mu, 0.1, el)
-        t_jac += time.perf_counter() - t0
-        done += len(el)
-    t_jac_full = t_jac * dg.Ne / done
-    # per stage the oracle's Newton evaluates about two Jacobians and a handful of residuals
-    t_stage = 2.0 * t_jac_full + 5.0 * t_res
-    return dict(value=dg.Nu / t_stage, t_res=t_res, t_jac_full=t_jac_full, elems=done, Ne=dg.Ne,
-                seconds=t_res + t_jac, threads=_threads())
+    ui = u + A[0, 0] * k
+    R = M @ k - dt * dg.residual(ui, mu, ti)
+    Ji = dg.jacobian(ui, mu, ti)
+    lu = spla.splu((M - A[0, 0] * dt * Ji).tocsc())
+    k = k - lu.solve(R)
+    t1 = time.perf_counter()
+    ui = u + A[0, 0] * k
+    g = w @ dg.dqoi_du(ui, mu, ti)
+    kap = lu.solve(b[0] * lam + dt * b[0] * A[0, 0] * g, trans="T")
+    lam_prev = lam + dt * (Ji.T @ kap) + dt * b[0] * g
+    grad = dt * (kap @ dg.dr_dmu(ui, mu, ti)) + dt * b[0] * (w @ dg.dqoi_dmu(ui, mu, ti))
+    t2 = time.perf_counter()
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    assert np.all(np.isfinite(lam_prev)) and np.all(np.isfinite(grad))
+    t_stage = 2.0 * (t1 - t0) + (t2 - t1)
+    return dict(value=dg.Nu / t_stage, Nu=dg.Nu, Ne=dg.Ne, t_iter=t1 - t0, t_adjoint=t2 - t1, seconds=t2 - t0,
+                cores=round(cpu / (t2 - t0), 2), stages=3 * c["Nt"], **cpu_info())
 
 
-def _threads():
-    try:
-        from threadpoolctl import threadpool_info
-        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        return 1
+def oracle_stage_text(s, config):
+    return (f"the oracle's stage unit on the full {config} mesh ({s['Ne']} elements, {s['Nu']} DOF), timed once: "
+            f"one stage-Newton iteration with Jacobian refresh (residual, complex-step block Jacobian, SuperLU "
+            f"factorization and solve: {s['t_iter']:.1f} s) and one adjoint stage with QoI and dF/dmu terms "
+            f"({s['t_adjoint']:.1f} s); extrapolated to a stage as 2 Newton iterations + 1 adjoint stage (a "
+            f"stage needs at least that, so the value is an upper bound on the oracle's speed; a period is "
+            f"{s['stages']} stages); NumPy/SciPy as they stand, {s['cores']} cores busy on average (CPU time / "
+            f"wall time); host: {s['nproc']} CPUs, {s['model']}")
+
+
+def start_oracle_stage(config):
+    """Runs oracle_stage in a fresh interpreter (started before any CUDA work) so that it
+    overlaps the GPU timing; collect() returns its result."""
+    import tempfile
+    fd, path = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-stage", config, "--out", path],
+                            stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True)
+
+    def collect():
+        _, err = proc.communicate()
+        try:
+            with open(path) as fh:
+                return json.load(fh)
+        except (OSError, ValueError):
+            return {"error": (err or "")[-400:]}
+        finally:
+            os.unlink(path)
+    return collect
 
 
 # --------------------------------------------------------------------------- ours
@@ -153,16 +210,20 @@ def max_over_ranks(x, device="cpu"):
 
 
 def l2_note(res, c, precision):
-    """Size of the stored linearization the sweeps stream against the 126 MB L2: per stage
-    and element about 16 nb x nb blocks of 8 bytes (FP64: Jacobian 4, inverse 1, folded 6,
-    transposes 5; mixed: FP64 Jacobian and transposes plus the FP32 copies, about the same)."""
+    """Where the timed sweeps' data lives against the 126 MB L2.  One stage solve re-applies
+    the same folded stage operator (3 nb^2 words per element) and block inverse (nb^2) over
+    its Krylov basis (restart + 1 vectors); successive stages stream new operators out of the
+    stored linearization of the whole period (about 16 nb^2 words per element and stage)."""
     p = c["p"]
     nb = 2 * (p + 1) * (p + 2)
-    word_blocks = 16 * 8
-    gb = res["ne"] * nb * nb * word_blocks * 3 * res["Nt"] / 1e9
-    if gb > 1.0:
-        return f"working set (stored stage linearization, ~{gb:.0f} GB) far larger than L2; no flush needed"
-    return f"working set ~{gb * 1e3:.0f} MB, not larger than L2: small-case timing, not a bench value"
+    word = 4 if precision == "mixed" else 8
+    op_mb = res["ne"] * 4 * nb * nb * word / 1e6
+    basis_mb = 41 * res["nu"] * 8 / 1e6
+    period_gb = res["ne"] * nb * nb * 16 * 8 * 3 * res["Nt"] / 1e9
+    where = "comparable to" if op_mb + basis_mb > 40 else "inside"
+    return (f"per stage solve: operator + inverse {op_mb:.0f} MB and Krylov basis {basis_mb:.0f} MB, {where} the "
+            f"126 MB L2 (re-read across the solve's Arnoldi steps, partly L2-resident); each step streams the "
+            f"period's stored linearization (~{period_gb:.0f} GB) from HBM, so no flush is needed between steps")
 
 
 def whole_job_value(units_per_rank, ms_max, world):
@@ -212,7 +273,9 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
-        A.pp_prof_select(args.roofline_kernel)
+        A.pp_prof_sample(PROF_STRIDE)
+        A.pp_prof_select(KERNELS[args.precision][0])
+        A.pp_prof_also(KERNELS[args.precision][1])
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -228,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
         clocks = clk.stop()
-        launches_k, kern_ms = A.pp_prof_read()
+        kern = {k: A.pp_prof_read_class(k) for k in KERNELS[args.precision]}
         iters = A.pp_sweep_counts(ctx)
         counts = A.pp_prof_counts()
         ms = ev0.elapsed_time(ev1) / args.steps
@@ -242,8 +305,9 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n_e2e = max(1, min(args.e2e_steps, args.steps))
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(n_e2e):
                 u0.copy_(host_u0, non_blocking=True)
                 A.pp_primal_period(ctx, m, mu, u0, Nt, u_final=uN)
                 A.pp_adjoint_sweep(ctx, lamN, lam0, weights=weights, n_mu=len(mu))
@@ -252,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
                 host_u0.copy_(host_uN)
             e1.record(stream)
             torch.cuda.synchronize()
-            e2e_ms = e0.elapsed_time(e1) / args.steps
+            e2e_ms = e0.elapsed_time(e1) / n_e2e
             e2e = dict(ms_per_step=e2e_ms, h2d=nu * 8, d2h=nu * 8 + 8 * len(mu))
 
     ms = max_over_ranks(ms, dev)
@@ -260,58 +324,59 @@ def run_ours(args, rank, world, local_rank):
         e2e["ms_per_step"] = max_over_ranks(e2e["ms_per_step"], dev)
     A.pp_mesh_destroy(m)
     A.pp_destroy(ctx)
-    return dict(config=args.config, ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, split=split, kern_launches=launches_k, kern_ms=kern_ms,
+    return dict(config=args.config, ms=ms, nu=nu, ne=ne, Nt=Nt, clocks=clocks, iters=iters, split=split, kern=kern,
                 counts=counts, e2e=e2e)
 
 
-def roofline_for(kernel, res, peaks, fp64_tflops, c):
-    """Algorithmic work per launch of the timed kernel class: FLOPs or bytes per element of
-    the kernel's definition times the elements one launch processes."""
+# kernel classes timed by the bench: (folded stage operator, Gram-Schmidt passes of an Arnoldi step)
+KERNELS = {"fp64": ("stage_op", "arnoldi"), "mixed": ("stage_op32", "arnoldi32")}
+PROF_STRIDE = 8   # one launch (one Arnoldi step) in 8 is bracketed by CUDA events
+
+
+def roofline_for(kernel, res, peaks, fp64_tflops, c, sustained):
+    """Roofline entry of one timed kernel class.  achieved = algorithmic work per launch (the
+    kernel's definition: FLOPs or bytes per element times the elements of one launch, or the
+    counted bytes of the Arnoldi passes) / the launch's average CUDA-event duration."""
     p = c["p"]
     Np = (p + 1) * (p + 2) // 2
     nb = 4 * Np
-    nqv, nqf = (p + 2) ** 2, p + 2
     ne = res["ne"]
-    if res["kern_launches"] <= 0:
+    launches, ms, counted = res["kern"][kernel]
+    if launches <= 0:
         return None
-    t = res["kern_ms"] / res["kern_launches"] * 1e-3
-    if kernel == "jacobian":
-        # basis contraction per variable pair (16 per element): W = C T over 3 trial types at
-        # 2 nqv Np volume and 2 x 3 nqf Np face entries, then J_ab = D W (Np^2 (2 nqv + 3 nqf)
-        # for the diagonal block, Np^2 nqf for each face block); 2 flops per FMA.  The dual-
-        # number flux derivatives are not counted.
-        w_fma = 3 * (2 * nqv * Np + 2 * 3 * nqf * Np)
-        j_fma = Np * Np * (2 * nqv + 3 * nqf) + 3 * Np * Np * nqf
-        flops = ne * 16 * 2 * (w_fma + j_fma)
+    t = ms / launches * 1e-3
+    hbm = peaks["hbm_gbs"]
+    if kernel.startswith("arnoldi"):
+        # bytes of one classical Gram-Schmidt pass over the basis, counted per Arnoldi step
+        # at launch (2k + 3) n words; 3 launches per step
+        ach = counted / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": "k_cgs<KB,%s> x3 (one Arnoldi orthogonalization step)"
+                % ("double" if kernel == "arnoldi" else "float"),
+                "launches": launches, "avg_us": t * 1e6, "algorithmic_bytes_per_launch": counted / launches,
+                "note": "basis of one stage solve (<= 41 x N_u words) is L2-resident: a low fraction means "
+                        "latency-bound grid reductions, not HBM"}
+    word = 4 if kernel.endswith("32") else 8
+    # folded operator: 3 blocks + 3 neighbour slices + own slice + output per element
+    byts = ne * (3 * nb * nb * word + 5 * nb * word)
+    if word == 8:
+        # GB300's FP64 FMA rate is below its HBM rate for a block product (one 8-byte word per
+        # FMA): the FP64 operator is held against the measured FP64 peak
+        flops = 2.0 * ne * 3 * nb * nb
         ach = flops / t / 1e12
         return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
                 "frac": ach / fp64_tflops if fp64_tflops else None,
                 "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
-                "kernel": "k_jacobian", "launches": res["kern_launches"], "avg_us": t * 1e6}
-    if kernel in ("stage_matvec", "block_apply", "stage_matvec32", "block_apply32", "stage_op", "stage_op32"):
-        blocks = 4 if kernel.startswith("stage_matvec") else (3 if kernel.startswith("stage_op") else 1)
-        word = 4 if kernel.endswith("32") else 8
-        # matrix blocks + input slices + output (stage_op: 3 neighbour slices, the element's own
-        # slice for the identity term and the output)
-        byts = ne * (blocks * nb * nb * word + (5 if kernel.startswith("stage_op") else 2) * nb * word)
-        if word == 8:
-            # GB300 issues ~2 FP64 FMA per clock per SM: the FP64 block product is FP64-ALU bound
-            # (its FMA floor exceeds its HBM floor), so it is held against the measured FP64 peak
-            flops = 2.0 * ne * blocks * nb * nb
-            ach = flops / t / 1e12
-            return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
-                    "frac": ach / fp64_tflops if fp64_tflops else None,
-                    "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
-                    "kernel": ("k_stream_rows<%d,3,double> (I + B, folded block-Jacobi)" % nb if kernel == "stage_op"
-                               else "k_" + kernel.replace("32", "") + "<double>"), "launches": res["kern_launches"],
-                    "avg_us": t * 1e6, "hbm_gbs_equiv": byts / t / 1e9}
-        ach = byts / t / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
-                "kernel": ("k_stream_rows<%d,3,float> (I + B, folded block-Jacobi)" % nb if kernel == "stage_op32"
-                           else "k_" + kernel.replace("32", "") + "<float>"),
-                "launches": res["kern_launches"], "avg_us": t * 1e6}
-    return None
+                "kernel": "k_stream_rows<%d,3,double> (I + B, folded block-Jacobi)" % nb,
+                "launches": launches, "avg_us": t * 1e6, "hbm_gbs_equiv": byts / t / 1e9,
+                "peak_source": "pp_measure_fp64_peak_clock (16-chain FMA probe, measured in this run)"}
+    ach = byts / t / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
+            "kernel": "k_stream_rows<%d,3,float> (I + B, folded block-Jacobi)" % nb,
+            "launches": launches, "avg_us": t * 1e6,
+            "note": "operator of one stage solve (~%d MB) is re-read across its Arnoldi steps and partly "
+                    "L2-resident" % (ne * 3 * nb * nb * word / 1e6)}
 
 
 def profile_step(args):
@@ -349,44 +414,45 @@ def profile_step(args):
 
 def main():
     args = parse()
+    if args.oracle_stage:
+        # helper mode of the cpu_baseline leg: one oracle stage, result as JSON in args.out
+        r = oracle_stage(args.oracle_stage)
+        with open(args.out, "w") as fh:
+            json.dump(r, fh)
+        return
     if args.profile_step > 0:
         profile_step(args)
         return
-    if args.roofline_kernel is None:
-        args.roofline_kernel = "stage_op32" if args.precision == "mixed" else "stage_op"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     from pp_inputs import CONFIGS
     c = CONFIGS[args.config]
     workload = (f"{args.config}: {2 * c['n_theta'] * c['n_r']}-triangle O-grid, p={c['p']}, "
-                f"{c['Nt']} DIRK3 steps/period, primal sweep + adjoint sweep (F = J_E, dF/dmu)")
+                f"{c['Nt']} DIRK3 steps/period, rigid-body mesh motion (Eq. defmap), CDG viscous terms; "
+                f"primal sweep + adjoint sweep (F = J_E, dF/dmu)")
 
     if args.impl == "reference":
         if rank != 0:
             return
+        # The oracle's unit of stage work takes about two minutes on a CPU at full size, so the
+        # run times it once: --steps and --warmup do not subdivide it (warm-up is the set-up).
         t0 = time.perf_counter()
-        vals = []
-        budget = max(5.0, 150.0 / max(args.steps + args.warmup, 1))
-        for i in range(args.warmup + args.steps):
-            s = oracle_sample(args.config, budget)
-            if i >= args.warmup:
-                vals.append(s["value"])
-        v = statistics.mean(vals)
+        s = oracle_stage(args.config)
+        v = s["value"]
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": workload},
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["threads"], "kind": "oracle",
-                                 "sample": f"per step: oracle residual + complex-step Jacobian rows on "
-                                           f"{s['elems']}/{s['Ne']} elements (~{budget:.0f} s), extrapolated "
-                                           "linearly to one stage-Newton iteration of the mesh; sparse LU "
-                                           "excluded (oracle cost understated)"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+                                 "sample": oracle_stage_text(s, args.config)},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": time.perf_counter() - t0}
         print(json.dumps(line))
         return
 
+    # the oracle's stage runs in its own process on the host cores while the GPU is timed
+    collect = start_oracle_stage(args.config) if (not args.no_cpu_baseline and world == 1) else None
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -401,18 +467,25 @@ def main():
     from paper_1512_00616_gb300 import api as A
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-    fp64 = A.pp_measure_fp64_peak(local_rank)
+    fp64, fp64_mhz = A.pp_measure_fp64_peak_clock(local_rank)
     units = res["nu"] * res["Nt"] * 3
     value = whole_job_value(units, res["ms"], world)
-    roof = roofline_for(args.roofline_kernel, res, peaks, fp64, c)
+    roofs = {k: roofline_for(k, res, peaks, fp64, c, False) for k in KERNELS[args.precision]}
+    # the dominant kernel: the class with the larger share of the timed region (timed launches only)
+    share = {k: res["kern"][k][1] for k in roofs}
+    dom = max(share, key=share.get)
+    other = [k for k in roofs if k != dom][0]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": workload, "precision": args.precision, "dof": res["nu"], "elements": res["ne"], "Nt": res["Nt"],
-                   "parallelism": f"replicas x{world}",
-                   "l2": l2_note(res, c, args.precision)},
-        "roofline": roof, "fp64_fma_peak_tflops_measured": fp64,
+        "config": {"workload": workload, "precision": args.precision, "dof": res["nu"], "elements": res["ne"],
+                   "Nt": res["Nt"], "parallelism": f"replicas x{world}", "l2": l2_note(res, c, args.precision)},
+        "roofline": roofs[dom],
+        "roofline_next": roofs[other],
+        "kernel_ms_timed": {k: res["kern"][k][1] for k in roofs},
+        "fp64_fma_peak": {"tflops": fp64, "sm_mhz_in_probe": fp64_mhz,
+                          "fma_per_clk_per_sm": (fp64 * 1e12 / 2 / (fp64_mhz * 1e6) / 152) if fp64_mhz else None},
         "clocks": res["clocks"],
         "gpu_launches": int(sum(res["counts"].values())),
         "launches_by_class": res["counts"],
@@ -423,12 +496,13 @@ def main():
         e = res["e2e"]
         line["e2e"] = {"value": whole_job_value(units, e["ms_per_step"], world), "unit": UNIT,
                        "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
-    if not args.no_cpu_baseline and world == 1:
-        s = oracle_sample(args.config, args.cpu_budget)
-        line["cpu_baseline"] = {"value": s["value"], "unit": UNIT, "cores": s["threads"], "kind": "oracle",
-                                "sample": f"oracle residual + complex-step Jacobian rows on {s['elems']}/{s['Ne']} "
-                                          f"elements ({s['seconds']:.1f} s), extrapolated linearly to one "
-                                          "stage (2 Jacobians + 5 residuals); sparse LU excluded"}
+    if collect is not None:
+        s = collect()
+        if "value" in s:
+            line["cpu_baseline"] = {"value": s["value"], "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+                                    "sample": oracle_stage_text(s, args.config)}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "kind": "oracle", "error": s.get("error")}
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -95,6 +95,9 @@ typedef struct pp_config {
      of stage data; tangent / adjoint sweeps recompute each segment from its checkpoint
      (identical iterates, so identical results) -- memory ~ Nt/K states + 3K stages. */
   int checkpoint_stride;
+  /* pp_shoot_nk: m >= 0 steps of Algorithm fixedpt (u0 <- u^(Nt)(u0)) before the Newton
+     iterations, the nonlinear preconditioning of Sec. 6.1 (0: none) */
+  int nk_fixed_point_pre;
 } pp_config;
 
 /* Fills *cfg with the paper's case (Sec. 6.1: gamma 1.4, Pr 0.72, Mach 0.2,
@@ -126,6 +129,23 @@ const char* pp_version(void);
 int pp_mesh_create(pp_ctx* ctx, const double* verts, int nv, const int32_t* tris, const int32_t* ftag,
                    int nt, pp_mesh** out);
 int pp_mesh_destroy(pp_mesh* mesh);
+
+/* Seeded O-grid around a symmetric 12%-thick 4-digit airfoil (closed trailing edge), the
+   synthetic stand-in for the paper's flapping-airfoil mesh (Sec. 6.1; the paper's mesh is
+   not published): n_theta wall points equally spaced in arc length counter-clockwise from
+   the trailing edge, far-field circle of radius r_far about (0.5, 0), n_r + 1 rings with
+   geometric stretching q = 1 + 4/n_r, interior vertices jittered by up to 10% of the
+   distance to their nearest grid neighbour with the counter-based SplitMix64 generator
+   (output c of seed s: state s + (c + 1) 0x9E3779B97F4A7C15, then the published finalizer;
+   u = -1 + 2 (x >> 11) 2^-53), each quad split into two counter-clockwise triangles.
+   Vertex (k, j) (wall index k, ring j) has index k (n_r + 1) + j; nv = n_theta (n_r + 1),
+   nt = 2 n_theta n_r.  pp_ogrid_generate is host code (no GPU, no context): verts HOST
+   [nv][2], tris and ftag HOST [nt][3] (any may be NULL; tags as in pp_mesh_create), nv and nt
+   receive the sizes.  pp_mesh_ogrid generates the mesh and creates it on ctx's device.
+   Errors: PP_EINVAL (n_theta < 3, n_r < 1, r_far <= 1), and those of pp_mesh_create. */
+int pp_ogrid_generate(int n_theta, int n_r, double r_far, uint64_t seed, double* verts, int32_t* tris,
+                      int32_t* ftag, int* nv, int* nt);
+int pp_mesh_ogrid(pp_ctx* ctx, int n_theta, int n_r, double r_far, uint64_t seed, pp_mesh** out);
 /* ne, np (nodes per element) and nu = ne*4*np; any output may be NULL. */
 int pp_mesh_info(const pp_mesh* mesh, int* ne, int* np, int64_t* nu);
 
@@ -222,6 +242,17 @@ typedef struct pp_shoot_stats {
 int pp_shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess, int Nt,
                 double tol, double* u0_out, double* qoi, pp_shoot_stats* stats);
 
+/* Fixed-point iteration for the periodic initial condition (Algorithm fixedpt): u0 <-
+   u^(Nt)(u0) from u0_guess until ||u^(Nt)(u0) - u0||_2 <= tol (Eq. fixedpt); converges when
+   the period map is a contraction (all Floquet multipliers inside the unit circle), at the
+   rate of the largest multiplier.  u0_guess, u0_out: DEVICE [N_u] (may alias).  qoi: HOST [4]
+   or NULL, as in pp_primal_period at the returned u0, whose linearization is stored on
+   return.  stats: HOST or NULL (newton_iters = fixed-point iterations, residual history,
+   primal_sweeps).  Errors: PP_ENOCONV after maxit iterations (u0_out holds the last iterate),
+   PP_ENAN. */
+int pp_shoot_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess,
+                         int Nt, double tol, int maxit, double* u0_out, double* qoi, pp_shoot_stats* stats);
+
 typedef struct pp_adj_stats {
   int krylov_iters;      /* adjoint sensitivity sweeps in the GMRES */
   double residual;       /* final ||lambda^(0)(lambda_Nt) - lambda_Nt||_2 */
@@ -236,6 +267,63 @@ typedef struct pp_adj_stats {
    periodic adjoint final condition).  Tolerance adj_tol from the config. */
 int pp_periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
                         const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats);
+
+/* The periodic adjoint problems of n_qoi QoIs (1..4) about one periodic orbit, solved
+   together by one restarted block GMRES: the operator Phi^T - I of Algorithm dual does not
+   depend on the QoI (Sec. 4), so the right-hand sides -d_q share one block Krylov space and
+   each block step applies it to n_qoi vectors.  Then for each QoI the gradient of Algorithm
+   grad.  weights: HOST [n_qoi][2], the (w_W, w_x) of each QoI (e.g. (1, 0) and (0, 1) for W
+   and J_x).  F: HOST [n_qoi] or NULL; dFdmu: HOST [n_qoi][n_mu]; lam_Nt: DEVICE
+   [n_qoi][N_u] or NULL; u0 as in pp_periodic_adjoint.  Tolerance adj_tol on each QoI's
+   ||lambda^(0)(x) - x||_2; block steps per restart: 64 / n_qoi - 1, limited by adj_restart
+   (adj_restart + 1 >= the basis size).  stats->krylov_iters counts all adjoint sweeps,
+   stats->residual is the largest final residual.  Errors: PP_ENOCONV, PP_EINVAL,
+   PP_ESTATE, PP_ENOMEM. */
+int pp_periodic_adjoint_multi(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                              int n_qoi, const double* weights, double* F, double* dFdmu, double* lam_Nt,
+                              pp_adj_stats* stats);
+
+/* Batched forms of pp_shoot_nk and pp_periodic_adjoint for n_batch parameter vectors (a
+   batch of mu for the derivative of a batched QoI, e.g. through an autograd function).
+   mu: HOST [n_batch][n_mu].  Device arrays hold one N_u block per batch entry:
+   u0_guess (or NULL), u0_out, u0, lam_Nt (or NULL): DEVICE [n_batch][N_u].  qoi: HOST
+   [n_batch][4] or NULL; stats: HOST [n_batch] or NULL; status: HOST [n_batch] or NULL
+   (per-entry status of the shooting); weights: HOST [n_batch][2] (one QoI weighting per
+   entry); F: HOST [n_batch] or NULL; dFdmu: HOST [n_batch][n_mu].
+   The entries run one after the other on the context's stream and reuse its stored
+   linearization: each mu needs its own linearization of the whole period (about 126 GB at
+   2048 elements, p = 3, 100 steps), so the batch does not fit in device memory at once.
+   pp_shoot_nk_batched returns PP_ENOCONV if an entry did not converge (the others still
+   run; see status); any other error stops the batch.  On return the stored linearization
+   is that of the last entry. */
+int pp_shoot_nk_batched(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, int n_batch,
+                        const double* u0_guess, int Nt, double tol, double* u0_out, double* qoi, pp_shoot_stats* stats,
+                        int* status);
+int pp_periodic_adjoint_batched(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, int n_batch,
+                                const double* u0, int Nt, const double* weights, double* F, double* dFdmu,
+                                double* lam_Nt, pp_adj_stats* stats);
+
+/* Floquet multipliers of the periodic orbit (Sec. 3.3, Eq. stab-def): m steps of Arnoldi
+   on Phi = du^(Nt)/du0 about the stored linearization (call pp_shoot_nk first, so that it
+   is the periodic orbit's), Phi applied by tangent sweeps (Eq. dirk-sens-mvp), with full
+   classical Gram-Schmidt reorthogonalization; the Ritz values of the m x m Hessenberg
+   matrix (Francis double-shift QR) approximate the largest-modulus multipliers first.  The
+   orbit is stable when every multiplier lies inside the unit circle.  wr, wi: HOST [m],
+   real and imaginary parts sorted by modulus, largest first.  hlast: HOST [1] or NULL,
+   h_(m+1,m) (0: the Krylov space is invariant and the values are exact).  Allocates an
+   (m+1) x N_u device basis for the call.  Errors: PP_ESTATE (no sweep stored), PP_EINVAL
+   (m outside [1, N_u]), PP_ENOMEM, PP_ENOCONV (QR iteration cap). */
+int pp_floquet(pp_ctx* ctx, int m, double* wr, double* wi, double* hlast);
+
+/* The periodic adjoint condition solved by fixed-point iteration (the dual fixed point of
+   Sec. 6.2 on Eq. fixedpt-dual): lambda_Nt <- lambda^(0)(lambda_Nt) from 0 until
+   ||lambda^(0)(lambda_Nt) - lambda_Nt||_2 <= tol, then the gradient of Algorithm grad with
+   the converged multipliers.  Arguments as pp_periodic_adjoint, plus tol and maxit;
+   stats->krylov_iters counts the adjoint sweeps of the iteration.  Errors: PP_ENOCONV,
+   PP_ENAN, PP_ESTATE. */
+int pp_periodic_adjoint_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0,
+                                    int Nt, const double* weights, double tol, int maxit, double* F, double* dFdmu,
+                                    double* lam_Nt, pp_adj_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -36,10 +36,13 @@ int pp_mse_f32(int n, const float* Y, const float* T, float* dY, float* loss, vo
 /* Adam step (step >= 1 counts from 1) on n parameters with moments m1, m2. */
 int pp_adam_f32(int n, float* w, const float* g, float* m1, float* m2, float lr, float b1, float b2, float eps,
                 int step, void* stream);
-/* Eigen-decomposition of a symmetric n x n matrix A (n <= 256, overwritten) by cyclic
-   Jacobi rotations in one thread block: V (n x n) receives the eigenvectors as columns,
-   w (n) the eigenvalues (unsorted); stops when the off-diagonal norm is <= tol times the
-   Frobenius norm or after max_sweeps.  sweeps: DEVICE int or NULL. */
+/* Eigen-decomposition of a symmetric n x n matrix A (n <= 4096, overwritten) by cyclic
+   Jacobi rotations in the parallel round-robin ordering: V (n x n) receives the eigenvectors
+   as columns, w (n) the eigenvalues (unsorted); stops when the off-diagonal norm is <= tol
+   times the Frobenius norm or after max_sweeps.  sweeps: DEVICE int or NULL.  n <= 256 runs
+   in one thread block with the test on the device; larger n runs one CTA per rotation pair
+   and round (columns, then rows), tests the norms on the host once per sweep (the call
+   then synchronizes the stream) and allocates (n + 2) doubles of device scratch. */
 int pp_syevj_f64(int n, double* A, double* V, double* w, double tol, int max_sweeps, int* sweeps, void* stream);
 
 #ifdef __cplusplus

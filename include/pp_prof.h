@@ -27,14 +27,28 @@ extern "C" {
 #define PP_K_STAGE_OP 11       /* FP64 stage operator with the preconditioner folded in, x + B x */
 #define PP_K_FOLD 12           /* products B = -c J_off D^-1 forming that operator (FP64 or FP32) */
 #define PP_K_STAGE_OP32 13     /* FP32 folded stage operator of the mixed-precision inner solves */
-#define PP_K_COUNT 14
+#define PP_K_ARNOLDI 14        /* the Gram-Schmidt passes of one FP64 Arnoldi step (3 launches) */
+#define PP_K_ARNOLDI32 15      /* the same in FP32 (mixed-precision inner solves) */
+#define PP_K_COUNT 16
 
-/* Starts timing every launch of kernel class `kind` (one class at a time; PP_K_NONE
-   stops).  Resets the accumulated totals.  Not thread-safe: one host thread drives libpp. */
+/* Starts timing every launch of kernel class `kind` (PP_K_NONE stops), and only that class.
+   Resets the accumulated totals of every class.  Not thread-safe: one host thread drives
+   libpp.  At most 262144 launches of a class are timed. */
 int pp_prof_select(int kind);
-/* Synchronizes the device and returns, for the selected class since pp_prof_select,
-   the number of launches and the summed event time in milliseconds. */
+/* Times one launch in `stride` of each timed class (default 1: every launch), so that the
+   events disturb the timed work less; classes that count bytes per group of launches (the
+   Arnoldi steps) are sampled by whole groups.  Applies from the next pp_prof_select. */
+int pp_prof_sample(int stride);
+/* Adds class `kind` to the timed classes without resetting the totals. */
+int pp_prof_also(int kind);
+/* Synchronizes the device and returns, for the class given to pp_prof_select, the number
+   of timed launches and their summed event time in milliseconds. */
 int pp_prof_read(int64_t* launches, double* total_ms);
+/* As pp_prof_read for any timed class, plus the algorithmic bytes of the timed launches
+   where the class counts them (PP_K_ARNOLDI*: (2k + 3) n words per Arnoldi step against k
+   basis vectors of length n: one classical Gram-Schmidt pass reads V and w for the
+   projections, then V and w again and writes w for the update and norm); 0 otherwise. */
+int pp_prof_read_class(int kind, int64_t* launches, double* total_ms, double* bytes);
 /* Counts launches of every class since the last pp_prof_select (no events). */
 int pp_prof_counts(int64_t* counts /* [PP_K_COUNT] */);
 
@@ -60,9 +74,17 @@ int pp_sweep_counts(const struct pp_ctx* ctx, int64_t* newton, int64_t* gmres_pr
 int pp_stage_apply(struct pp_ctx* ctx, int step, int stage, int kind, int trans, int prec, const double* x,
                    double* y);
 
-/* Measures the device's FP64 FMA throughput (TFLOP/s, 2 flops per FMA) with an
-   unrolled dependent-chain kernel over all SMs; returns PP_OK or PP_ECUDA. */
+/* All eigenvalues of an n x n upper Hessenberg matrix H (HOST, row-major, leading dimension
+   ld >= n; overwritten) by the Francis double-shift QR iteration used by pp_floquet; host
+   code only (no GPU needed).  wr, wi: HOST [n].  Returns PP_OK, PP_EINVAL or PP_ENOCONV. */
+int pp_hessenberg_eigvals(int n, double* H, int ld, double* wr, double* wi);
+
+/* Measures the device's FP64 FMA throughput (TFLOP/s, 2 flops per FMA): 16 independent FMA
+   chains per thread, 2048 threads per SM, about 0.2 s per run, best of 5 runs.  sm_mhz
+   (nullable) receives the SM clock of the best run, measured inside the kernel from the SM
+   cycle counter against the global timer.  Returns PP_OK or PP_ECUDA. */
 int pp_measure_fp64_peak(int device, double* tflops);
+int pp_measure_fp64_peak_clock(int device, double* tflops, double* sm_mhz);
 
 #ifdef __cplusplus
 }

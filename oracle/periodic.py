@@ -16,6 +16,10 @@ Plain, step-by-step statements of Sec. 3-4 of the paper:
                         linear system (du^(Nt)/du0 - I) du = R, the reading of
                         Eq. jac-prim).
 * ``periodic_adjoint`` / ``periodic_gradient`` -- Algorithm dual / Algorithm grad.
+* ``shoot_fixed_point`` -- Algorithm fixedpt; ``shoot_nk(m_pre=m)`` -- Newton-Krylov
+                        after m fixed-point steps (the nonlinear preconditioning of
+                        Sec. 6.1); ``periodic_adjoint_fixed_point`` -- the dual fixed
+                        point on Eq. fixedpt-dual.
 
 The QoI functional is F = w_W W + w_x J_x for weights (w_W, w_x).  F depends
 on the stages only, so dF/du^(Nt) = 0 and the periodic adjoint condition
@@ -202,9 +206,28 @@ def gmres(matvec, rhs, x0=None, tol=1e-10, restart=50, maxit=1000):
             return x, nmv, hist
 
 
-def shoot_nk(dg, mu, u0, Nt, tol=1e-10, gmres_rtol=1e-8, max_newton=30):
-    """Algorithm primal: Newton on R(u0) = u^(Nt)(u0) - u0 with matrix-free GMRES."""
+def shoot_fixed_point(dg, mu, u0, Nt, tol=1e-10, maxit=500):
+    """Algorithm fixedpt: u0 <- u^(Nt)(u0) until ||u^(Nt)(u0) - u0||_2 <= tol (Eq. fixedpt).
+    Returns (u0, trajectory from u0, residual history)."""
     u0 = np.array(u0, dtype=np.float64).reshape(-1)
+    history = []
+    for _ in range(maxit + 1):
+        tr = primal_sweep(dg, mu, u0, Nt)
+        rn = np.linalg.norm(tr.u[-1] - u0)
+        history.append(rn)
+        if rn <= tol:
+            return u0, tr, history
+        u0 = tr.u[-1].copy()
+    raise RuntimeError("oracle fixed-point iteration did not converge")
+
+
+def shoot_nk(dg, mu, u0, Nt, tol=1e-10, gmres_rtol=1e-8, max_newton=30, m_pre=0):
+    """Algorithm primal: Newton on R(u0) = u^(Nt)(u0) - u0 with matrix-free GMRES.  m_pre > 0
+    first takes m_pre steps of Algorithm fixedpt (u0 <- u^(Nt)(u0)), the nonlinear
+    preconditioning of Sec. 6.1."""
+    u0 = np.array(u0, dtype=np.float64).reshape(-1)
+    for _ in range(m_pre):
+        u0 = primal_sweep(dg, mu, u0, Nt, store=False).u[-1].copy()
     history = []
     for _ in range(max_newton + 1):
         tr = primal_sweep(dg, mu, u0, Nt)
@@ -227,6 +250,21 @@ def periodic_adjoint(dg, tr, weights, tol=1e-12):
     d, _ = adjoint_sweep(dg, tr, np.zeros(dg.Nu), weights)
     x, _, _ = gmres(lambda v: adjoint_sweep(dg, tr, v)[0] - v, -d, tol=tol)
     return x
+
+
+def periodic_adjoint_fixed_point(dg, tr, weights, tol=1e-12, maxit=2000):
+    """The periodic adjoint condition (Eq. fixedpt-dual, with dF/du^(Nt) = 0 here) solved by
+    fixed-point iteration x <- lambda^(0)(x), from x = 0.  Returns (x, residual history)."""
+    x = np.zeros(dg.Nu)
+    history = []
+    for _ in range(maxit + 1):
+        y, _ = adjoint_sweep(dg, tr, x, weights)
+        rn = np.linalg.norm(y - x)
+        history.append(rn)
+        if rn <= tol:
+            return x, history
+        x = y
+    raise RuntimeError("oracle dual fixed-point iteration did not converge")
 
 
 def periodic_gradient(dg, tr, weights, tol=1e-12):

@@ -27,13 +27,17 @@ EXPORTED = [
     "pp_steady_state",
     # include/pp_prof.h
     "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
-    "pp_stage_apply",
+    "pp_shoot_fixed_point", "pp_periodic_adjoint_fixed_point", "pp_floquet", "pp_hessenberg_eigvals",
+    "pp_ogrid_generate", "pp_mesh_ogrid", "pp_shoot_nk_batched", "pp_periodic_adjoint_batched",
+    "pp_periodic_adjoint_multi",
+    "pp_stage_apply", "pp_prof_also", "pp_prof_sample", "pp_prof_read_class", "pp_measure_fp64_peak_clock",
     # include/pp_learn.h
     "pp_gemm_f32", "pp_gemm_f64", "pp_bias_act_f32", "pp_gelu_backward_f32", "pp_colsum_f32", "pp_mse_f32",
     "pp_adam_f32", "pp_syevj_f64",
 ]
 PP_K = dict(none=0, jacobian=1, residual=2, stage_matvec=3, block_apply=4, block_inverse=5, krylov=6, other=7,
-            stage_matvec32=8, block_apply32=9, krylov32=10, stage_op=11, fold=12, stage_op32=13)
+            stage_matvec32=8, block_apply32=9, krylov32=10, stage_op=11, fold=12, stage_op32=13, arnoldi=14,
+            arnoldi32=15)
 
 
 class pp_config(C.Structure):
@@ -44,7 +48,8 @@ class pp_config(C.Structure):
                 ("lin_rtol", C.c_double), ("nk_gmres_rtol", C.c_double), ("nk_restart", C.c_int),
                 ("nk_max_newton", C.c_int), ("nk_max_krylov", C.c_int), ("adj_tol", C.c_double),
                 ("adj_restart", C.c_int), ("adj_maxit", C.c_int), ("precision", C.c_int),
-                ("inner_maxit", C.c_int), ("inner_rtol", C.c_double), ("checkpoint_stride", C.c_int)]
+                ("inner_maxit", C.c_int), ("inner_rtol", C.c_double), ("checkpoint_stride", C.c_int),
+                ("nk_fixed_point_pre", C.c_int)]
 
 
 class pp_shoot_stats(C.Structure):
@@ -88,12 +93,26 @@ def _load():
         "pp_adjoint_sweep": (I, [P, P, dp, P, dp]),
         "pp_shoot_nk": (I, [P, P, dp, I, P, I, D, P, dp, C.POINTER(pp_shoot_stats)]),
         "pp_periodic_adjoint": (I, [P, P, dp, I, P, I, dp, dp, dp, P, C.POINTER(pp_adj_stats)]),
+        "pp_shoot_fixed_point": (I, [P, P, dp, I, P, I, D, I, P, dp, C.POINTER(pp_shoot_stats)]),
+        "pp_floquet": (I, [P, I, dp, dp, dp]),
+        "pp_periodic_adjoint_multi": (I, [P, P, dp, I, P, I, I, dp, dp, dp, P, C.POINTER(pp_adj_stats)]),
+        "pp_shoot_nk_batched": (I, [P, P, dp, I, I, P, I, D, P, dp, C.POINTER(pp_shoot_stats), C.POINTER(I)]),
+        "pp_periodic_adjoint_batched": (I, [P, P, dp, I, I, P, I, dp, dp, dp, P, C.POINTER(pp_adj_stats)]),
+        "pp_ogrid_generate": (I, [I, I, D, C.c_uint64, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                  C.POINTER(I), C.POINTER(I)]),
+        "pp_mesh_ogrid": (I, [P, I, I, D, C.c_uint64, C.POINTER(P)]),
+        "pp_hessenberg_eigvals": (I, [I, dp, I, dp, dp]),
+        "pp_periodic_adjoint_fixed_point": (I, [P, P, dp, I, P, I, dp, D, I, dp, dp, P, C.POINTER(pp_adj_stats)]),
         "pp_prof_select": (I, [I]),
         "pp_prof_read": (I, [C.POINTER(C.c_int64), dp]),
         "pp_prof_counts": (I, [C.POINTER(C.c_int64)]),
         "pp_measure_fp64_peak": (I, [I, dp]),
         "pp_sweep_counts": (I, [P] + [C.POINTER(C.c_int64)] * 4),
         "pp_stage_apply": (I, [P, I, I, I, I, I, P, P]),
+        "pp_prof_also": (I, [I]),
+        "pp_prof_sample": (I, [I]),
+        "pp_prof_read_class": (I, [I, C.POINTER(C.c_int64), dp, dp]),
+        "pp_measure_fp64_peak_clock": (I, [I, dp, dp]),
         "pp_gemm_f32": (I, [I, I, I, C.c_float, P, I, I, P, I, I, C.c_float, P, I, P]),
         "pp_gemm_f64": (I, [I, I, I, D, P, I, I, P, I, I, D, P, I, P]),
         "pp_bias_act_f32": (I, [I, I, P, P, P, I, P]),
@@ -179,6 +198,27 @@ def pp_mesh_create(ctx, verts, tris, ftag):
     return h
 
 
+def pp_ogrid_generate(n_theta, n_r, r_far=10.0, seed=0):
+    """(verts [nv, 2], tris [nt, 3], ftag [nt, 3]) of the library's seeded O-grid (host code)."""
+    nv, nt = C.c_int(), C.c_int()
+    code = _lib.pp_ogrid_generate(int(n_theta), int(n_r), float(r_far), int(seed), None, None, None,
+                                  C.byref(nv), C.byref(nt))
+    if code != PP_OK:
+        raise PPError(code, "pp_ogrid_generate")
+    v = np.zeros((nv.value, 2))
+    t = np.zeros((nt.value, 3), dtype=np.int32)
+    g = np.zeros((nt.value, 3), dtype=np.int32)
+    _lib.pp_ogrid_generate(int(n_theta), int(n_r), float(r_far), int(seed), v.ctypes.data_as(C.POINTER(C.c_double)),
+                           t.ctypes.data_as(C.POINTER(C.c_int32)), g.ctypes.data_as(C.POINTER(C.c_int32)), None, None)
+    return v, t, g
+
+
+def pp_mesh_ogrid(ctx, n_theta, n_r, r_far=10.0, seed=0):
+    out = C.c_void_p()
+    _check(ctx, _lib.pp_mesh_ogrid(ctx, int(n_theta), int(n_r), float(r_far), int(seed), C.byref(out)))
+    return out
+
+
 def pp_mesh_destroy(mesh):
     _check(None, _lib.pp_mesh_destroy(mesh))
 
@@ -251,6 +291,69 @@ def pp_shoot_nk(ctx, mesh, mu, Nt, tol, u0_out, u0_guess=None, raise_on_noconv=T
     return qoi, stats
 
 
+def pp_shoot_nk_batched(ctx, mesh, mu, Nt, tol, u0_out, u0_guess=None, raise_on_noconv=True):
+    """mu [B, n_mu] (host); u0_out, u0_guess: CUDA float64 [B * N_u].  Returns (qoi [B, 4], status [B], stats)."""
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    B, n_mu = m.shape
+    qoi = np.zeros((B, 4))
+    st = (pp_shoot_stats * B)()
+    status = (C.c_int * B)()
+    code = _lib.pp_shoot_nk_batched(ctx, mesh, m.ctypes.data_as(C.POINTER(C.c_double)), n_mu, B,
+                                    _dev(u0_guess, "u0_guess"), int(Nt), float(tol), _dev(u0_out, "u0_out"),
+                                    qoi.ctypes.data_as(C.POINTER(C.c_double)), st, status)
+    if code != PP_ENOCONV or raise_on_noconv:
+        _check(ctx, code)
+    stats = [dict(newton_iters=s.newton_iters, krylov_iters=s.krylov_iters, cold_start=s.cold_start,
+                  residual=list(s.residual[:min(s.newton_iters + 1, 64)]), seconds=s.seconds) for s in st]
+    return qoi, np.array(status[:]), stats
+
+
+def pp_periodic_adjoint_batched(ctx, mesh, mu, Nt, weights, u0, lam_Nt=None):
+    """mu [B, n_mu], weights [B, 2] (host); u0, lam_Nt: CUDA float64 [B * N_u].  Returns (F [B], dF/dmu [B, n_mu])."""
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    B, n_mu = m.shape
+    w = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), (B, 2)))
+    F = np.zeros(B)
+    g = np.zeros((B, n_mu))
+    st = (pp_adj_stats * B)()
+    _check(ctx, _lib.pp_periodic_adjoint_batched(ctx, mesh, m.ctypes.data_as(C.POINTER(C.c_double)), n_mu, B,
+                                                 _dev(u0, "u0"), int(Nt), w.ctypes.data_as(C.POINTER(C.c_double)),
+                                                 F.ctypes.data_as(C.POINTER(C.c_double)),
+                                                 g.ctypes.data_as(C.POINTER(C.c_double)), _dev(lam_Nt, "lam_Nt"), st))
+    return F, g
+
+
+def pp_periodic_adjoint_multi(ctx, mesh, mu, Nt, weights, u0=None, lam_Nt=None):
+    """weights [n_qoi, 2]; lam_Nt: CUDA float64 [n_qoi * N_u] or None.  Returns (F [n_qoi],
+    dF/dmu [n_qoi, n_mu], stats)."""
+    m, mp = _host(mu)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    nq = w.shape[0]
+    F = np.zeros(nq)
+    g = np.zeros((nq, len(m)))
+    st = pp_adj_stats()
+    _check(ctx, _lib.pp_periodic_adjoint_multi(ctx, mesh, mp, len(m), _dev(u0, "u0"), int(Nt), nq,
+                                               w.ctypes.data_as(C.POINTER(C.c_double)),
+                                               F.ctypes.data_as(C.POINTER(C.c_double)),
+                                               g.ctypes.data_as(C.POINTER(C.c_double)), _dev(lam_Nt, "lam_Nt"),
+                                               C.byref(st)))
+    return F, g, dict(sweeps=st.krylov_iters, residual=st.residual, seconds=st.seconds)
+
+
+def pp_shoot_fixed_point(ctx, mesh, mu, Nt, tol, maxit, u0_guess, u0_out, raise_on_noconv=True):
+    m, mp = _host(mu)
+    qoi = np.zeros(4)
+    st = pp_shoot_stats()
+    code = _lib.pp_shoot_fixed_point(ctx, mesh, mp, len(m), _dev(u0_guess, "u0_guess"), int(Nt), float(tol),
+                                     int(maxit), _dev(u0_out, "u0_out"), qoi.ctypes.data_as(C.POINTER(C.c_double)),
+                                     C.byref(st))
+    if code != PP_ENOCONV or raise_on_noconv:
+        _check(ctx, code)
+    n = min(st.newton_iters + 1, 64)
+    return qoi, dict(iterations=st.newton_iters, primal_sweeps=st.primal_sweeps, residual=list(st.residual[:n]),
+                     seconds=st.seconds, status=code)
+
+
 def pp_steady_state(ctx, mesh, mu, u, tol=1e-10, maxit=100):
     m, mp = _host(mu)
     steps, rel = C.c_int(), C.c_double()
@@ -272,6 +375,39 @@ def pp_periodic_adjoint(ctx, mesh, mu, Nt, weights, u0=None, lam_Nt=None):
     return float(F[0]), g, dict(krylov_iters=st.krylov_iters, residual=st.residual, seconds=st.seconds)
 
 
+def pp_periodic_adjoint_fixed_point(ctx, mesh, mu, Nt, weights, tol, maxit, u0=None, lam_Nt=None):
+    m, mp = _host(mu)
+    w, wp = _host(weights)
+    F = np.zeros(1)
+    g = np.zeros(len(m))
+    st = pp_adj_stats()
+    _check(ctx, _lib.pp_periodic_adjoint_fixed_point(ctx, mesh, mp, len(m), _dev(u0, "u0"), int(Nt), wp, float(tol),
+                                                     int(maxit), F.ctypes.data_as(C.POINTER(C.c_double)),
+                                                     g.ctypes.data_as(C.POINTER(C.c_double)),
+                                                     _dev(lam_Nt, "lam_Nt"), C.byref(st)))
+    return float(F[0]), g, dict(sweeps=st.krylov_iters, residual=st.residual, seconds=st.seconds)
+
+
+def pp_floquet(ctx, m):
+    """Ritz values (complex, largest modulus first) of Phi from m Arnoldi steps, and h_(m+1,m)."""
+    wr, wi, hl = np.zeros(m), np.zeros(m), np.zeros(1)
+    _check(ctx, _lib.pp_floquet(ctx, int(m), wr.ctypes.data_as(C.POINTER(C.c_double)),
+                                wi.ctypes.data_as(C.POINTER(C.c_double)), hl.ctypes.data_as(C.POINTER(C.c_double))))
+    return wr + 1j * wi, float(hl[0])
+
+
+def pp_hessenberg_eigvals(H):
+    """Eigenvalues of an upper Hessenberg matrix (host code of the library)."""
+    A = np.array(H, dtype=np.float64, order="C", copy=True)
+    n = A.shape[0]
+    wr, wi = np.zeros(n), np.zeros(n)
+    code = _lib.pp_hessenberg_eigvals(n, A.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                      wr.ctypes.data_as(C.POINTER(C.c_double)), wi.ctypes.data_as(C.POINTER(C.c_double)))
+    if code != PP_OK:
+        raise PPError(code, "pp_hessenberg_eigvals")
+    return wr + 1j * wi
+
+
 # --------------------------------------------------------------------------- diagnostics (include/pp_prof.h)
 def pp_prof_select(kind):
     k = PP_K[kind] if isinstance(kind, str) else int(kind)
@@ -284,8 +420,25 @@ def pp_prof_read():
     return n.value, ms.value
 
 
+def pp_prof_sample(stride):
+    _check(None, _lib.pp_prof_sample(int(stride)))
+
+
+def pp_prof_also(kind):
+    k = PP_K[kind] if isinstance(kind, str) else int(kind)
+    _check(None, _lib.pp_prof_also(k))
+
+
+def pp_prof_read_class(kind):
+    """(timed launches, summed ms, algorithmic bytes) of one timed kernel class."""
+    k = PP_K[kind] if isinstance(kind, str) else int(kind)
+    n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+    _check(None, _lib.pp_prof_read_class(k, C.byref(n), C.byref(ms), C.byref(by)))
+    return n.value, ms.value, by.value
+
+
 def pp_prof_counts():
-    a = (C.c_int64 * 14)()
+    a = (C.c_int64 * len(PP_K))()
     _check(None, _lib.pp_prof_counts(a))
     return {k: a[v] for k, v in PP_K.items() if k != "none"}
 
@@ -294,6 +447,13 @@ def pp_measure_fp64_peak(device=0):
     t = C.c_double()
     _check(None, _lib.pp_measure_fp64_peak(int(device), C.byref(t)))
     return t.value
+
+
+def pp_measure_fp64_peak_clock(device=0):
+    """(TFLOP/s, SM MHz inside the probe)."""
+    t, mhz = C.c_double(), C.c_double()
+    _check(None, _lib.pp_measure_fp64_peak_clock(int(device), C.byref(t), C.byref(mhz)))
+    return t.value, mhz.value
 
 
 def pp_sweep_counts(ctx):

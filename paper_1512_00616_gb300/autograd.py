@@ -3,7 +3,8 @@
 Forward: for every motion vector of the batch, Newton-Krylov shooting (Algorithm primal)
 to a periodic initial state (warm-started by a callable or by the previous solution),
 then the cycle-averaged flapping energy J_E = -W/T and thrust J_T = -J_x/T (Eq. qoi).
-Backward: one periodic adjoint per batch entry (Algorithms dual and grad) for
+Backward: the periodic adjoint of every batch entry in one batched call
+(pp_periodic_adjoint_batched; Algorithms dual and grad) for
 F = g_E J_E + g_T J_T, i.e. weights (-g_E/T, -g_T/T) on (W, J_x); the linearization
 is recomputed from the saved periodic state by a primal sweep (checkpointed every K
 steps when the context's checkpoint_stride is K > 0).  Every step runs in libpp; this
@@ -76,9 +77,11 @@ class PeriodicQoI(torch.autograd.Function):
         g = grad_out.detach().cpu().numpy().astype(np.float64)
         solver = ctx.solver
         grads = np.zeros_like(ctx.mus)
-        for b, (m, u0) in enumerate(zip(ctx.mus, ctx.u0s)):
-            if not np.any(g[b]):
-                continue
-            w = np.array([-g[b, 0] / solver.T, -g[b, 1] / solver.T])
-            _, grads[b] = solver.gradient(m, u0, w)
+        live = [b for b in range(len(ctx.mus)) if np.any(g[b])]
+        if live:
+            # one batched call: the periodic adjoint of every live entry (pp_periodic_adjoint_batched)
+            w = np.stack([[-g[b, 0] / solver.T, -g[b, 1] / solver.T] for b in live])
+            u0 = torch.cat([ctx.u0s[b] for b in live])
+            _, gl = A.pp_periodic_adjoint_batched(solver.ctx, solver.mesh, ctx.mus[live], solver.Nt, w, u0)
+            grads[live] = gl
         return torch.tensor(grads, dtype=torch.float64, device=grad_out.device), None

@@ -12,9 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpp.so")
-SOURCES = ["dg_kernels.cu", "linalg_kernels.cu", "learn_kernels.cu", "prof.cu", "noalloc.cu", "stream_kernels.cu", "host.cpp", "solver.cpp"]
+SOURCES = ["dg_kernels.cu", "linalg_kernels.cu", "learn_kernels.cu", "prof.cu", "noalloc.cu", "stream_kernels.cu", "host.cpp", "solver.cpp", "floquet.cpp", "mesh_gen.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(HERE, "..", "include")]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(HERE, "..", "include")]
 
 
 def nvcc():

@@ -11,7 +11,7 @@ struct pp_mesh {
   pp_ctx* ctx = nullptr;
   int ne = 0;
   double* d_real = nullptr;  // one allocation for all FP64 geometry arrays
-  int* d_int = nullptr;      // one allocation for nbr, nbrface, tag
+  int* d_int = nullptr;      // one allocation for nbr, nbrface, tag, side
   pp::DevMesh dev{};
 };
 
@@ -20,7 +20,7 @@ namespace pp {
 // Reference-element tables computed on the host (see host.cpp).
 struct RefHost {
   int p = 0, Np = 0, nb = 0, nqv = 0, nqf = 0;
-  std::vector<double> phi_v, dphi_v, w_v, xi_v, phi_f, dphi_f, xi_f, w_f, Mref;
+  std::vector<double> phi_v, dphi_v, w_v, xi_v, phi_f, dphi_f, xi_f, w_f, Mref, lift_v, lift_f;
 };
 
 // Krylov workspace of one GMRES level (stage solves and the outer shooting /
@@ -145,6 +145,14 @@ int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const
 int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
                      const double* weights, double* F, double* dFdmu, double* lam_Nt, pp_adj_stats* stats);
 int stage_apply(pp_ctx* ctx, int step, int i, int kind, int trans, int prec, const double* x, double* y);
+int periodic_adjoint_multi(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                           int n_qoi, const double* weights, double* F, double* dFdmu, double* lam_Nt,
+                           pp_adj_stats* stats);
+int shoot_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess,
+                      int Nt, double tol, int maxit, double* u0_out, double* qoi, pp_shoot_stats* stats);
+int periodic_adjoint_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0,
+                                 int Nt, const double* weights, double tol, int maxit, double* F, double* dFdmu,
+                                 double* lam_Nt, pp_adj_stats* stats);
 }  // namespace pp
 
 #define PP_CK(...)                                                                                   \

@@ -7,9 +7,13 @@
 // Numerical fluxes (the paper defers them to its references; readings):
 //  - inviscid: Roe's approximate Riemann solver applied to the ALE normal flux
 //    F(U).n - (v_G.n) U, Harten entropy fix with delta = 0.1 c;
-//  - viscous: interior penalty {F_vis}.n + sigma (U+ - U-);
-//  - wall: no-slip, adiabatic; ghost state with the mesh velocity; exact
-//    no-penetration inviscid flux;  far field: free-stream ghost state.
+//  - viscous: the compact discontinuous Galerkin (CDG) scheme of Sec. 6: liftings of
+//    the face jumps U_hat - U- into the element (the lifted gradients are formed by the
+//    kernels from the reference lifting tables); on an interior face the element with
+//    the smaller index supplies the viscous flux F_vis(U_S, grad U_S + r_f) . n with the
+//    lifting of that face only; boundary faces add the penalty c11 (U_hat - U-);
+//  - wall: no-slip, adiabatic; wall state with the mesh velocity; exact
+//    no-penetration inviscid flux;  far field: free-stream state.
 //
 // Every function is templated on the scalar type so that the same code gives
 // values (double) and exact directional derivatives (Dual).
@@ -141,45 +145,54 @@ __device__ __forceinline__ void roe_flux(const T UL[4], const T UR[4], const T n
   for (int a = 0; a < 4; ++a) out[a] = 0.5 * (FL[a] + FR[a]) - 0.5 * (l3 * D[a] + G1 * ev1[a] + G2 * ev2[a]);
 }
 
-// Numerical flux H (outward from the "-" element, per unit length) at one face point.
-// tag 0 interior (Up, dUp used), 1 wall, 2 far field.
+// No-slip wall state: the interior density and internal energy, moving with the wall.
 template <class T>
-__device__ __forceinline__ void face_flux(int tag, const T Um[4], const T dUm[4][2], const T Up[4],
-                                          const T dUp[4][2], const T n[2], const T vG[2], double sigma,
-                                          const Phys& ph, T H[4]) {
-  T vn = vG[0] * n[0] + vG[1] * n[1];
-  T Fvm[4][2];
+__device__ __forceinline__ void wall_state(const T Um[4], const T vG[2], T Ub[4]) {
+  T r = Um[0];
+  T eint = Um[3] / r - 0.5 * (Um[1] * Um[1] + Um[2] * Um[2]) / (r * r);
+  Ub[0] = r;
+  Ub[1] = r * vG[0];
+  Ub[2] = r * vG[1];
+  Ub[3] = r * (eint + 0.5 * (vG[0] * vG[0] + vG[1] * vG[1]));
+}
+
+// Face value U_hat of U at one face point: the neighbour trace (tag 0), the wall state
+// (tag 1) or the free stream (tag 2).
+template <class T>
+__device__ __forceinline__ void face_value(int tag, const T Um[4], const T Up[4], const T vG[2], const Phys& ph,
+                                           T Uh[4]) {
   if (tag == 1) {
-    // no-slip adiabatic wall: ghost shares density and internal energy, moves with the wall
-    T r = Um[0];
-    T eint = Um[3] / r - 0.5 * (Um[1] * Um[1] + Um[2] * Um[2]) / (r * r);
-    T Ub[4] = {r, r * vG[0], r * vG[1], r * (eint + 0.5 * (vG[0] * vG[0] + vG[1] * vG[1]))};
-    T Fn[4];
-    normal_flux(Ub, n, vn, ph.gam, Fn);
-    viscous_flux(Ub, dUm, ph, true, Fvm);
+    wall_state(Um, vG, Uh);
+  } else if (tag == 0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-      H[a] = Fn[a] - (Fvm[a][0] * n[0] + Fvm[a][1] * n[1] + sigma * (Ub[a] - Um[a]));
-    return;
-  }
-  viscous_flux(Um, dUm, ph, false, Fvm);
-  if (tag == 0) {
-    T Fvp[4][2];
-    viscous_flux(Up, dUp, ph, false, Fvp);
-    T R[4];
-    roe_flux(Um, Up, n, vn, ph.gam, R);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-      H[a] = R[a] - (0.5 * ((Fvm[a][0] + Fvp[a][0]) * n[0] + (Fvm[a][1] + Fvp[a][1]) * n[1]) +
-                     sigma * (Up[a] - Um[a]));
+    for (int a = 0; a < 4; ++a) Uh[a] = Up[a];
   } else {
-    T Ui[4] = {T(ph.Uinf[0]), T(ph.Uinf[1]), T(ph.Uinf[2]), T(ph.Uinf[3])};
-    T R[4];
-    roe_flux(Um, Ui, n, vn, ph.gam, R);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-      H[a] = R[a] - (Fvm[a][0] * n[0] + Fvm[a][1] * n[1] + sigma * (Ui[a] - Um[a]));
+    for (int a = 0; a < 4; ++a) Uh[a] = T(ph.Uinf[a]);
   }
+}
+
+// CDG numerical flux H (outward from the "-" element, per unit length) at one face point:
+//   H = H_inv(U-, U+) - F_vis(U_S, Q_S) . n - c11 (U_hat - U-)
+// with H_inv Roe's flux (interior, far field) or the exact wall flux, and Q_S the lifted
+// gradient of the side S that supplies the viscous flux (side = 1: this element, whose
+// viscous state is U- or, on the wall, the wall state; side = 0: the neighbour, U+).
+// The wall flux is adiabatic (zero heat flux); c11 is zero on interior faces.
+template <class T>
+__device__ __forceinline__ void face_flux(int tag, int side, const T Um[4], const T Up[4], const T QS[4][2],
+                                          const T n[2], const T vG[2], double c11, const Phys& ph, T H[4]) {
+  T vn = vG[0] * n[0] + vG[1] * n[1];
+  T Hi[4], Uh[4], Fv[4][2];
+  face_value(tag, Um, Up, vG, ph, Uh);
+  if (tag == 1) {
+    normal_flux(Uh, n, vn, ph.gam, Hi);
+    viscous_flux(Uh, QS, ph, true, Fv);
+  } else {
+    roe_flux(Um, Uh, n, vn, ph.gam, Hi);
+    viscous_flux(side ? Um : Up, QS, ph, false, Fv);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) H[a] = Hi[a] - (Fv[a][0] * n[0] + Fv[a][1] * n[1] + c11 * (Uh[a] - Um[a]));
 }
 
 }  // namespace pp

@@ -131,6 +131,51 @@ static RefHost build_tables(int p) {
   for (int q = 0; q < r.nqv; ++q)
     for (int i = 0; i < r.Np; ++i)
       for (int j = 0; j < r.Np; ++j) r.Mref[i * r.Np + j] += r.w_v[q] * r.phi_v[q * r.Np + i] * r.phi_v[q * r.Np + j];
+  // CDG lifting tables: Minv by Gauss-Jordan (the reference mass matrix is SPD), then
+  // E_f[j][q] = sum_i Minv[j][i] phi_i(f, q) w_q, the nodal coefficients of the lifting of a
+  // unit jump at face point q, evaluated at the volume and at the face-f points
+  const int Np = r.Np, nqv = r.nqv, nqf = r.nqf;
+  std::vector<double> A(r.Mref), Minv(Np * Np, 0.0);
+  for (int i = 0; i < Np; ++i) Minv[i * Np + i] = 1.0;
+  for (int k = 0; k < Np; ++k) {
+    const double d = 1.0 / A[k * Np + k];
+    for (int j = 0; j < Np; ++j) {
+      A[k * Np + j] *= d;
+      Minv[k * Np + j] *= d;
+    }
+    for (int i = 0; i < Np; ++i) {
+      if (i == k) continue;
+      const double f = A[i * Np + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < Np; ++j) {
+        A[i * Np + j] -= f * A[k * Np + j];
+        Minv[i * Np + j] -= f * Minv[k * Np + j];
+      }
+    }
+  }
+  r.lift_v.assign(3 * nqv * nqf, 0.0);
+  r.lift_f.assign(3 * nqf * nqf, 0.0);
+  std::vector<double> E(Np * nqf);
+  for (int f = 0; f < 3; ++f) {
+    for (int j = 0; j < Np; ++j)
+      for (int q = 0; q < nqf; ++q) {
+        double s = 0.0;
+        for (int i = 0; i < Np; ++i) s += Minv[j * Np + i] * r.phi_f[(f * nqf + q) * Np + i];
+        E[j * nqf + q] = s * r.w_f[q];
+      }
+    for (int qv = 0; qv < nqv; ++qv)
+      for (int q = 0; q < nqf; ++q) {
+        double s = 0.0;
+        for (int j = 0; j < Np; ++j) s += r.phi_v[qv * Np + j] * E[j * nqf + q];
+        r.lift_v[(f * nqv + qv) * nqf + q] = s;
+      }
+    for (int qf = 0; qf < nqf; ++qf)
+      for (int q = 0; q < nqf; ++q) {
+        double s = 0.0;
+        for (int j = 0; j < Np; ++j) s += r.phi_f[(f * nqf + qf) * Np + j] * E[j * nqf + q];
+        r.lift_f[(f * nqf + qf) * nqf + q] = s;
+      }
+  }
   return r;
 }
 
@@ -259,7 +304,8 @@ int ensure_workspace(pp_ctx* ctx, const pp_mesh* mesh) {
   cudaFree(ctx->d_elem);
   ctx->d_J = ctx->d_Ainv = ctx->d_vec = ctx->d_elem = nullptr;
   const size_t nb2 = (size_t)ctx->tb.nb * ctx->tb.nb;
-  ctx->n_vec = 27;  // 0-8 primal, 9-15 tangent, 14-23 adjoint, 24-26 shooting / periodic adjoint
+  ctx->n_vec = 30;  // 0-8 primal, 9-15 tangent, 14-23 adjoint, 24-26 shooting / periodic adjoint,
+                    // 27-29 warm starts of the linear stage solves
   if (cudaMalloc(&ctx->d_J, sizeof(double) * mesh->ne * 4 * nb2) != cudaSuccess ||
       cudaMalloc(&ctx->d_Ainv, sizeof(double) * mesh->ne * nb2) != cudaSuccess ||
       cudaMalloc(&ctx->d_vec, sizeof(double) * ctx->n_vec * nu) != cudaSuccess ||
@@ -425,7 +471,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       !(cfg->Mach > 0) || (cfg->kin != PP_KIN_HEAVE_PITCH && cfg->kin != PP_KIN_FOURIER6) ||
       (cfg->precision != PP_PREC_FP64 && cfg->precision != PP_PREC_MIXED) ||
       (cfg->precision == PP_PREC_MIXED && (cfg->inner_maxit < 1 || cfg->inner_maxit > 60)) ||
-      cfg->checkpoint_stride < 0)
+      cfg->checkpoint_stride < 0 || cfg->nk_fixed_point_pre < 0)
     return PP_EINVAL;
   {
     // the launch set-up cached by the kernels' host wrappers is per process: one device
@@ -458,7 +504,8 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
     return off;
   };
   size_t o_phv = put(r.phi_v), o_dphv = put(r.dphi_v), o_wv = put(r.w_v), o_xiv = put(r.xi_v), o_phf = put(r.phi_f),
-         o_dphf = put(r.dphi_f), o_xif = put(r.xi_f), o_wf = put(r.w_f), o_M = put(r.Mref);
+         o_dphf = put(r.dphi_f), o_xif = put(r.xi_f), o_wf = put(r.w_f), o_M = put(r.Mref), o_lv = put(r.lift_v),
+         o_lf = put(r.lift_f);
   if (cudaMalloc(&ctx->d_tables, sizeof(double) * all.size()) != cudaSuccess) return fail(PP_ENOMEM);
   if (cudaMemcpy(ctx->d_tables, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(PP_ECUDA);
@@ -477,6 +524,8 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   tb.xi_f = ctx->d_tables + o_xif;
   tb.w_f = ctx->d_tables + o_wf;
   tb.Mref = ctx->d_tables + o_M;
+  tb.lift_v = ctx->d_tables + o_lv;
+  tb.lift_f = ctx->d_tables + o_lf;
   Phys& ph = ctx->ph;
   ph.gam = cfg->gamma;
   ph.Pr = cfg->Pr;
@@ -579,7 +628,9 @@ int pp_mesh_create(pp_ctx* ctx, const double* verts, int nv, const int32_t* tris
       return set_error(ctx, PP_EINVAL, "pp_mesh_create: face tags inconsistent with connectivity");
   }
   // geometry
-  std::vector<double> X0(2 * nt), B(4 * nt), BinvT(4 * nt), detB(nt), N(6 * nt), L(3 * nt), sigma(3 * nt);
+  std::vector<double> X0(2 * nt), B(4 * nt), BinvT(4 * nt), detB(nt), N(6 * nt), L(3 * nt), s_own(3 * nt),
+      s_nbr(3 * nt), c11(3 * nt);
+  std::vector<int> side(3 * nt);
   for (int e = 0; e < nt; ++e) {
     const double* v0 = verts + 2 * tris[3 * e];
     const double* v1 = verts + 2 * tris[3 * e + 1];
@@ -609,14 +660,18 @@ int pp_mesh_create(pp_ctx* ctx, const double* verts, int nv, const int32_t* tris
       N[6 * e + 2 * f + 1] = -tx / len;
     }
   }
+  // CDG data: lifting scales, boundary penalty C11 = 10 mu / h (h = detB / |f|), and the side
+  // that lifts each face (the element itself on the boundary, the lower index inside)
   const double mu = 1.0 / ctx->cfg.Re;
   for (int e = 0; e < nt; ++e)
     for (int f = 0; f < 3; ++f) {
-      double am = 0.5 * detB[e];
-      int e2 = nbr[3 * e + f];
-      double ap = e2 >= 0 ? 0.5 * detB[e2] : am;
-      sigma[3 * e + f] = 2.0 * mu * (p + 1) * (p + 1) * L[3 * e + f] / (am < ap ? am : ap);
+      const int i = 3 * e + f, e2 = nbr[i];
+      s_own[i] = L[i] / detB[e];
+      s_nbr[i] = e2 >= 0 ? L[i] / detB[e2] : s_own[i];
+      c11[i] = e2 >= 0 ? 0.0 : 10.0 * mu * L[i] / detB[e];
+      side[i] = (e2 < 0 || e2 > e) ? 1 : 0;
     }
+  (void)p;
   pp_mesh* m = new pp_mesh();
   m->ctx = ctx;
   m->ne = nt;
@@ -626,11 +681,13 @@ int pp_mesh_create(pp_ctx* ctx, const double* verts, int nv, const int32_t* tris
     real.insert(real.end(), v.begin(), v.end());
     return o;
   };
-  size_t oX0 = put(X0), oB = put(B), oBi = put(BinvT), od = put(detB), oN = put(N), oL = put(L), os = put(sigma);
+  size_t oX0 = put(X0), oB = put(B), oBi = put(BinvT), od = put(detB), oN = put(N), oL = put(L), oso = put(s_own),
+         osn = put(s_nbr), oc = put(c11);
   std::vector<int> ints;
   ints.insert(ints.end(), nbr.begin(), nbr.end());
   ints.insert(ints.end(), nbrface.begin(), nbrface.end());
   ints.insert(ints.end(), tag.begin(), tag.end());
+  ints.insert(ints.end(), side.begin(), side.end());
   if (cudaSetDevice(ctx->device) != cudaSuccess ||
       cudaMalloc(&m->d_real, sizeof(double) * real.size()) != cudaSuccess ||
       cudaMalloc(&m->d_int, sizeof(int) * ints.size()) != cudaSuccess) {
@@ -651,10 +708,13 @@ int pp_mesh_create(pp_ctx* ctx, const double* verts, int nv, const int32_t* tris
   d.detB = m->d_real + od;
   d.N = m->d_real + oN;
   d.L = m->d_real + oL;
-  d.sigma = m->d_real + os;
+  d.s_own = m->d_real + oso;
+  d.s_nbr = m->d_real + osn;
+  d.c11 = m->d_real + oc;
   d.nbr = m->d_int;
   d.nbrface = m->d_int + 3 * nt;
   d.tag = m->d_int + 6 * nt;
+  d.side = m->d_int + 9 * nt;
   *out = m;
   return PP_OK;
 }
@@ -773,6 +833,70 @@ int pp_periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int 
   PP_TRY(check_mu(ctx, n_mu));
   PP_CK(cudaSetDevice(ctx->device));
   return periodic_adjoint(ctx, mesh, mu, n_mu, u0, Nt, weights, F, dFdmu, lam_Nt, stats);
+}
+
+int pp_shoot_nk_batched(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, int n_batch,
+                        const double* u0_guess, int Nt, double tol, double* u0_out, double* qoi, pp_shoot_stats* stats,
+                        int* status) {
+  if (!ctx || !mesh || !mu || !u0_out || n_batch < 1 || Nt < 1 || !(tol > 0))
+    return set_error(ctx, PP_EINVAL, "pp_shoot_nk_batched: bad argument");
+  PP_TRY(check_mu(ctx, n_mu));
+  PP_CK(cudaSetDevice(ctx->device));
+  const int64_t nu = mesh_nu(ctx, mesh);
+  int first = PP_OK;
+  for (int b = 0; b < n_batch; ++b) {
+    const int st = shoot_nk(ctx, mesh, mu + (size_t)b * n_mu, n_mu, u0_guess ? u0_guess + (size_t)b * nu : nullptr, Nt,
+                            tol, u0_out + (size_t)b * nu, qoi ? qoi + 4 * (size_t)b : nullptr,
+                            stats ? stats + b : nullptr);
+    if (status) status[b] = st;
+    if (st != PP_OK && st != PP_ENOCONV) return st;
+    if (st != PP_OK && first == PP_OK) first = st;
+  }
+  return first;
+}
+
+int pp_periodic_adjoint_batched(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, int n_batch,
+                                const double* u0, int Nt, const double* weights, double* F, double* dFdmu,
+                                double* lam_Nt, pp_adj_stats* stats) {
+  if (!ctx || !mesh || !mu || !u0 || !weights || !dFdmu || n_batch < 1 || Nt < 1)
+    return set_error(ctx, PP_EINVAL, "pp_periodic_adjoint_batched: bad argument");
+  PP_TRY(check_mu(ctx, n_mu));
+  PP_CK(cudaSetDevice(ctx->device));
+  const int64_t nu = mesh_nu(ctx, mesh);
+  for (int b = 0; b < n_batch; ++b)
+    PP_TRY(periodic_adjoint(ctx, mesh, mu + (size_t)b * n_mu, n_mu, u0 + (size_t)b * nu, Nt, weights + 2 * (size_t)b,
+                            F ? F + b : nullptr, dFdmu + (size_t)b * n_mu, lam_Nt ? lam_Nt + (size_t)b * nu : nullptr,
+                            stats ? stats + b : nullptr));
+  return PP_OK;
+}
+
+int pp_periodic_adjoint_multi(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                              int n_qoi, const double* weights, double* F, double* dFdmu, double* lam_Nt,
+                              pp_adj_stats* stats) {
+  if (!ctx || !mesh || !mu || !weights || !dFdmu || Nt < 1 || n_qoi < 1 || n_qoi > 4)
+    return set_error(ctx, PP_EINVAL, "pp_periodic_adjoint_multi: bad argument");
+  PP_TRY(check_mu(ctx, n_mu));
+  PP_CK(cudaSetDevice(ctx->device));
+  return periodic_adjoint_multi(ctx, mesh, mu, n_mu, u0, Nt, n_qoi, weights, F, dFdmu, lam_Nt, stats);
+}
+
+int pp_shoot_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess,
+                         int Nt, double tol, int maxit, double* u0_out, double* qoi, pp_shoot_stats* stats) {
+  if (!ctx || !mesh || !mu || !u0_guess || !u0_out || Nt < 1 || !(tol > 0) || maxit < 0)
+    return set_error(ctx, PP_EINVAL, "pp_shoot_fixed_point: bad argument");
+  PP_TRY(check_mu(ctx, n_mu));
+  PP_CK(cudaSetDevice(ctx->device));
+  return shoot_fixed_point(ctx, mesh, mu, n_mu, u0_guess, Nt, tol, maxit, u0_out, qoi, stats);
+}
+
+int pp_periodic_adjoint_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0,
+                                    int Nt, const double* weights, double tol, int maxit, double* F, double* dFdmu,
+                                    double* lam_Nt, pp_adj_stats* stats) {
+  if (!ctx || !mesh || !mu || !weights || !dFdmu || Nt < 1 || !(tol > 0) || maxit < 0)
+    return set_error(ctx, PP_EINVAL, "pp_periodic_adjoint_fixed_point: bad argument");
+  PP_TRY(check_mu(ctx, n_mu));
+  PP_CK(cudaSetDevice(ctx->device));
+  return periodic_adjoint_fixed_point(ctx, mesh, mu, n_mu, u0, Nt, weights, tol, maxit, F, dFdmu, lam_Nt, stats);
 }
 
 int pp_stage_apply(pp_ctx* ctx, int step, int stage, int kind, int trans, int prec, const double* x, double* y) {

@@ -211,6 +211,104 @@ __global__ void __launch_bounds__(256) k_syevj(int n, double* A, double* V, doub
   if (tid == 0 && sweeps_done) *sweeps_done = sweep;
 }
 
+// ---- multi-CTA cyclic Jacobi for n > 256 (same ordering and rotations as k_syevj).
+// Round r of the round-robin tournament pairs the m = n (+1 if odd) indices into m/2
+// disjoint (p, q).  Columns phase: one CTA per pair computes the pair's rotation from
+// A_pp, A_qq, A_pq -- entries of columns p and q, which only this CTA changes in this
+// phase -- then rotates columns p, q of A and V over all rows.  Rows phase: one CTA per
+// pair rotates rows p, q of A with the stored rotation.
+__device__ __forceinline__ void round_pair(int m, int round, int pr, int& p, int& q) {
+  int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (m - 1);
+  int b = 1 + (m - 2 - pr + round) % (m - 1);
+  p = a < b ? a : b;
+  q = a < b ? b : a;
+}
+
+__global__ void __launch_bounds__(512) k_jacobi_cols(int n, int m, int round, double* A, double* V, double* cs,
+                                                     double* sn) {
+  const int pr = blockIdx.x;
+  int p, q;
+  round_pair(m, round, pr, p, q);
+  __shared__ double s_c, s_s;
+  if (threadIdx.x == 0) {
+    double c = 1.0, s = 0.0;
+    if (q < n) {
+      const double apq = A[(size_t)p * n + q];
+      if (apq != 0.0) {
+        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        c = 1.0 / sqrt(1.0 + t * t);
+        s = t * c;
+      }
+    }
+    s_c = c;
+    s_s = s;
+    cs[pr] = c;
+    sn[pr] = s;
+  }
+  __syncthreads();
+  if (q >= n) return;
+  const double c = s_c, s = s_s;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double ap = A[(size_t)r * n + p], aq = A[(size_t)r * n + q];
+    A[(size_t)r * n + p] = c * ap - s * aq;
+    A[(size_t)r * n + q] = s * ap + c * aq;
+    const double vp = V[(size_t)r * n + p], vq = V[(size_t)r * n + q];
+    V[(size_t)r * n + p] = c * vp - s * vq;
+    V[(size_t)r * n + q] = s * vp + c * vq;
+  }
+}
+
+__global__ void __launch_bounds__(512) k_jacobi_rows(int n, int m, int round, double* A, const double* cs,
+                                                     const double* sn) {
+  const int pr = blockIdx.x;
+  int p, q;
+  round_pair(m, round, pr, p, q);
+  if (q >= n) return;
+  const double c = cs[pr], s = sn[pr];
+  for (int col = threadIdx.x; col < n; col += blockDim.x) {
+    const double ap = A[(size_t)p * n + col], aq = A[(size_t)q * n + col];
+    A[(size_t)p * n + col] = c * ap - s * aq;
+    A[(size_t)q * n + col] = s * ap + c * aq;
+  }
+}
+
+// out[0] = off-diagonal sum of squares, out[1] = Frobenius sum of squares (one CTA, fixed order)
+__global__ void __launch_bounds__(1024) k_jacobi_norms(int n, const double* A, double* out) {
+  __shared__ double r0[1024], r1[1024];
+  double off = 0.0, all = 0.0;
+  for (int64_t i = threadIdx.x; i < (int64_t)n * n; i += blockDim.x) {
+    const double a = A[i];
+    all += a * a;
+    if (i / n != i % n) off += a * a;
+  }
+  r0[threadIdx.x] = off;
+  r1[threadIdx.x] = all;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      r0[threadIdx.x] += r0[threadIdx.x + o];
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = r0[0];
+    out[1] = r1[0];
+  }
+}
+
+__global__ void k_jacobi_finish(int n, const double* A, double* w, int* sweeps, int sw) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = A[(size_t)i * n + i];
+  if (sweeps && blockIdx.x == 0 && threadIdx.x == 0) *sweeps = sw;
+}
+
+__global__ void k_identity(int n, double* V) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * n; i += (int64_t)gridDim.x * blockDim.x)
+    V[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
 int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -273,10 +371,58 @@ int pp_adam_f32(int n, float* w, const float* g, float* m1, float* m2, float lr,
 }
 
 int pp_syevj_f64(int n, double* A, double* V, double* w, double tol, int max_sweeps, int* sweeps, void* stream) {
-  if (n <= 0 || n > 256 || !A || !V || !w) return PP_LEARN_EINVAL;
-  pp::ProfScope ps(PP_K_OTHER, (cudaStream_t)stream);
-  k_syevj<<<1, 256, 0, (cudaStream_t)stream>>>(n, A, V, w, tol, max_sweeps, sweeps);
-  return cudaGetLastError() == cudaSuccess ? 0 : PP_LEARN_ECUDA;
+  using namespace pp;
+  if (n <= 0 || n > 4096 || !A || !V || !w) return PP_LEARN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n <= 256) {
+    ProfScope ps(PP_K_OTHER, st);
+    k_syevj<<<1, 256, 0, st>>>(n, A, V, w, tol, max_sweeps, sweeps);
+    return cudaGetLastError() == cudaSuccess ? 0 : PP_LEARN_ECUDA;
+  }
+  // multi-CTA sweeps, the convergence test on the host once per sweep
+  const int m = (n + 1) / 2 * 2;
+  double* scratch = nullptr;  // cs [m/2] | sn [m/2] | norms [2]
+  if (cudaMalloc(&scratch, sizeof(double) * (m + 2)) != cudaSuccess) return PP_LEARN_ECUDA;
+  double* cs = scratch;
+  double* sn = scratch + m / 2;
+  double* nrm = scratch + m;
+  double h[2] = {0.0, 0.0};
+  int sweep = 0, rc = 0;
+  {
+    ProfScope ps(PP_K_OTHER, st);
+    k_identity<<<blocks_for((int64_t)n * n, 256), 256, 0, st>>>(n, V);
+  }
+  for (;; ++sweep) {
+    {
+      ProfScope ps(PP_K_OTHER, st);
+      k_jacobi_norms<<<1, 1024, 0, st>>>(n, A, nrm);
+    }
+    if (cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = PP_LEARN_ECUDA;
+      break;
+    }
+    if (sweep >= max_sweeps || sqrt(h[0]) <= tol * sqrt(h[1])) break;
+    for (int round = 0; round < m - 1; ++round) {
+      {
+        ProfScope ps(PP_K_OTHER, st);
+        k_jacobi_cols<<<m / 2, 512, 0, st>>>(n, m, round, A, V, cs, sn);
+      }
+      ProfScope ps(PP_K_OTHER, st);
+      k_jacobi_rows<<<m / 2, 512, 0, st>>>(n, m, round, A, cs, sn);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = PP_LEARN_ECUDA;
+      break;
+    }
+  }
+  if (rc == 0) {
+    ProfScope ps(PP_K_OTHER, st);
+    k_jacobi_finish<<<blocks_for(n, 256), 256, 0, st>>>(n, A, w, sweeps, sweep);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = PP_LEARN_ECUDA;
+  }
+  cudaFree(scratch);
+  return rc;
 }
 
 }  // extern "C"

@@ -643,6 +643,20 @@ __device__ __forceinline__ bool cgs_finish(int nk, const double* bp, double* par
   return true;
 }
 
+// Second Gram-Schmidt pass needed?  |w - V h1|^2 = |w|^2 - |h1|^2 in exact arithmetic; the
+// pass is repeated when more than half of |w|^2 cancelled (|w - V h1| < |w| / sqrt 2).  Every
+// caller (every CTA of every pass) evaluates the same expression on the same coefficients in
+// the same order, so all take the same decision.  Warp 0 of the block calls it; returns
+// |h1|^2 in hh.
+__device__ __forceinline__ bool reorth_needed_warp0(const double* h1, double w2, int k, double& hh) {
+  double s = 0.0;
+  for (int t = threadIdx.x; t < k; t += 32) s += h1[t] * h1[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  hh = s;
+  return !(s <= 0.5 * w2);
+}
+
 template <class S>
 struct CgsArgs {
   int mode;           // 0 dots, 1 update + dots, 2 update + norm, 3 single dot
@@ -675,15 +689,11 @@ __global__ void __launch_bounds__(CGS_T, 1) k_cgs(CgsArgs<S> a) {
   int mode = a.mode;
   bool to_norm = false;
   if (a.chk) {
-    // second pass needed?  |w - V h1|^2 = |w|^2 - |h1|^2 in exact arithmetic; the pass is
-    // repeated when more than half of |w|^2 cancelled (|w - V h1| < |w| / sqrt 2).  Every
-    // CTA takes the same decision from the same first-pass coefficients.
+    // second pass needed?  (same decision in every CTA, see reorth_needed_warp0)
     if (threadIdx.x < 32) {
-      double hh = 0.0;
-      for (int t = threadIdx.x; t < k; t += 32) hh += a.chk[t] * a.chk[t];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
-      if (threadIdx.x == 0) s_need = (hh <= 0.5 * a.chk[k]) ? 0 : 1;
+      double hh;
+      const bool nd = reorth_needed_warp0(a.chk, a.chk[k], k, hh);
+      if (threadIdx.x == 0) s_need = nd ? 1 : 0;
     }
     __syncthreads();
     const bool need = s_need != 0;
@@ -980,8 +990,8 @@ int cgs_blocks(int64_t n) {
 }
 
 template <class S>
-cudaError_t launch_cgs(const CgsArgs<S>& a, cudaStream_t st) {
-  ProfScope ps(sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32, st);
+cudaError_t launch_cgs(const CgsArgs<S>& a, cudaStream_t st, int kind = -1) {
+  ProfScope ps(kind >= 0 ? kind : (sizeof(S) == 8 ? PP_K_KRYLOV : PP_K_KRYLOV32), st);
   if (a.k < 1 || a.k > CGS_MAXK) return cudaErrorInvalidValue;
   const int g = cgs_blocks(a.n);
   switch ((a.k + 3) / 4) {
@@ -1056,22 +1066,26 @@ cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w
                                  double* nrm, double* partial, unsigned* counter, int j, int m, double* H, double* cs,
                                  double* sn, double* g, double* stat, cudaStream_t st) {
   const GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat};
+  const int kind = sizeof(S) == 8 ? PP_K_ARNOLDI : PP_K_ARNOLDI32;
+  // algorithmic traffic of one classical Gram-Schmidt pass: V and w read for the projections,
+  // V and w read and w written for the update and norm
+  prof_add_bytes(kind, (2.0 * k + 3.0) * (double)n * sizeof(S), 3);
   // pass 1: h1 = V^T w and |w|^2
   CgsArgs<S> a = cgs_args<S>(0, n, V, ldv, k, nullptr, w, h1, partial, counter);
   a.self = 1;
-  cudaError_t e = launch_cgs<S>(a, st);
+  cudaError_t e = launch_cgs<S>(a, st, kind);
   if (e != cudaSuccess) return e;
   // pass 2: w -= V h1; then h2 = V^T w if reorthogonalization is needed, else |w|^2 + Givens
   a = cgs_args<S>(1, n, V, ldv, k, h1, w, h2, partial, counter);
   a.chk = h1;
   a.out_nrm = nrm;
   a.gv = gv;
-  if ((e = launch_cgs<S>(a, st)) != cudaSuccess) return e;
+  if ((e = launch_cgs<S>(a, st, kind)) != cudaSuccess) return e;
   // pass 3 (only if needed): w -= V h2, |w|^2 + Givens
   a = cgs_args<S>(2, n, V, ldv, k, h2, w, nrm, partial, counter);
   a.chk = h1;
   a.gv = gv;
-  return launch_cgs<S>(a, st);
+  return launch_cgs<S>(a, st, kind);
 }
 
 template <class S>

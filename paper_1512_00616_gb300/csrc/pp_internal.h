@@ -93,6 +93,11 @@ struct DevTables {
   const double* xi_f;    // [3][nqf][2]
   const double* w_f;     // [nqf], sum 1
   const double* Mref;    // [Np][Np]
+  // CDG liftings on the reference element: the scalar lifting l of a jump given at the
+  // points of face f, l = sum_j phi_j (Mref^-1 c)_j with c_i = sum_q w_q phi_i(f, q) jump_q,
+  // evaluated at the volume points (lift_v) and at the points of face f itself (lift_f)
+  const double* lift_v;  // [3][nqv][nqf]
+  const double* lift_f;  // [3][nqf][nqf]
 };
 
 struct DevMesh {
@@ -103,7 +108,11 @@ struct DevMesh {
   const double* detB;    // [ne]
   const double* N;       // [ne][3][2] reference outward unit normals
   const double* L;       // [ne][3]   face lengths
-  const double* sigma;   // [ne][3]   interior-penalty coefficients
+  const double* s_own;   // [ne][3]   |f| / detB_e  (lifting scale of face f into e)
+  const double* s_nbr;   // [ne][3]   |f| / detB of the neighbour (interior faces)
+  const double* c11;     // [ne][3]   boundary penalty 10 mu |f| / detB_e (0 on interior faces)
+  const int* side;       // [ne][3]   1: e lifts face f and supplies its viscous flux (boundary
+                         //           faces, and interior faces whose neighbour has a larger index)
   const int* nbr;        // [ne][3]   neighbour or -1
   const int* nbrface;    // [ne][3]
   const int* tag;        // [ne][3]   0 interior, 1 wall, 2 far field

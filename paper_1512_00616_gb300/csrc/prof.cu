@@ -1,5 +1,6 @@
 // Kernel-class timing with CUDA events on the launching stream, launch counting,
-// and an FP64 FMA throughput probe (diagnostics declared in include/pp_prof.h).
+// algorithmic byte counts, and an FP64 FMA throughput probe (diagnostics declared in
+// include/pp_prof.h).
 #include <vector>
 
 #include "../../include/pp_prof.h"
@@ -8,56 +9,111 @@
 namespace pp {
 
 namespace {
-int g_kind = PP_K_NONE;
-std::vector<cudaEvent_t> g_ev;   // pairs (start, stop)
-size_t g_used = 0;               // events used
+struct ClassTiming {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+  size_t used = 0;              // events used
+  int64_t timed = 0;
+  double bytes = 0.0;
+  int64_t seen = 0;             // launches seen (sampling of single launches)
+  int64_t groups = 0;           // launch groups seen (sampling of counted groups)
+  int pending = 0;              // launches of a sampled group still to time
+  int skip = 0;                 // launches of an unsampled group still to skip
+};
+constexpr size_t kMaxPairs = 1 << 18;
+int g_stride = 1;               // time one launch (or counted group) in g_stride
+int g_primary = PP_K_NONE;
+ClassTiming g_cls[PP_K_COUNT];
 int64_t g_launch[PP_K_COUNT] = {0};
-int64_t g_timed = 0;
-constexpr size_t kMaxPairs = 1 << 16;
+
+void reset_all() {
+  for (int k = 0; k < PP_K_COUNT; ++k) {
+    g_cls[k].on = false;
+    g_cls[k].used = 0;
+    g_cls[k].timed = 0;
+    g_cls[k].bytes = 0.0;
+    g_cls[k].seen = g_cls[k].groups = 0;
+    g_cls[k].pending = g_cls[k].skip = 0;
+    g_launch[k] = 0;
+  }
+}
 }  // namespace
 
 void prof_begin(int kind, cudaStream_t st, cudaEvent_t* stop_out) {
   g_launch[kind]++;
   *stop_out = nullptr;
-  if (kind != g_kind || g_used + 2 > 2 * kMaxPairs) return;
-  if (g_used + 2 > g_ev.size()) {
+  ClassTiming& c = g_cls[kind];
+  if (!c.on) return;
+  bool take;
+  if (c.pending > 0) {
+    take = true;
+    --c.pending;
+  } else if (c.skip > 0) {
+    take = false;
+    --c.skip;
+  } else {
+    take = (c.seen++ % g_stride) == 0;
+  }
+  if (!take || c.used + 2 > 2 * kMaxPairs) return;
+  if (c.used + 2 > c.ev.size()) {
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return;
     if (cudaEventCreate(&b) != cudaSuccess) {
       cudaEventDestroy(a);
       return;
     }
-    g_ev.push_back(a);
-    g_ev.push_back(b);
+    c.ev.push_back(a);
+    c.ev.push_back(b);
   }
-  cudaEventRecord(g_ev[g_used], st);
-  *stop_out = g_ev[g_used + 1];
-  g_used += 2;
-  g_timed++;
+  cudaEventRecord(c.ev[c.used], st);
+  *stop_out = c.ev[c.used + 1];
+  c.used += 2;
+  c.timed++;
 }
 
 void prof_end(cudaEvent_t stop, cudaStream_t st) {
   if (stop) cudaEventRecord(stop, st);
 }
 
-__global__ void k_fma_probe(double* out, int iters) {
-  double a0 = threadIdx.x * 1e-9, a1 = a0 + 1e-9, a2 = a0 + 2e-9, a3 = a0 + 3e-9;
-  double a4 = a0 + 4e-9, a5 = a0 + 5e-9, a6 = a0 + 6e-9, a7 = a0 + 7e-9;
+void prof_add_bytes(int kind, double bytes, int launches) {
+  ClassTiming& c = g_cls[kind];
+  if (!c.on) return;
+  if ((c.groups++ % g_stride) == 0 && c.used + 2 * (size_t)launches <= 2 * kMaxPairs) {
+    c.pending = launches;
+    c.bytes += bytes;
+  } else {
+    c.pending = 0;
+    c.skip = launches;
+  }
+}
+
+// 16 independent FMA chains per thread; thread 0 of block 0 reads the SM cycle counter and
+// the global timer (ns) around its loop, which gives the SM clock during the run.
+__global__ void k_fma_probe(double* out, long long* clk, int iters) {
+  double a[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[k] = threadIdx.x * 1e-9 + k * 1e-9;
   const double b = 0.999999999, c = 1e-12;
+  long long c0 = 0, t0 = 0;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    c0 = clock64();
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  }
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      a0 = fma(a0, b, c);
-      a1 = fma(a1, b, c);
-      a2 = fma(a2, b, c);
-      a3 = fma(a3, b, c);
-      a4 = fma(a4, b, c);
-      a5 = fma(a5, b, c);
-      a6 = fma(a6, b, c);
-      a7 = fma(a7, b, c);
-    }
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int k = 0; k < 16; ++k) a[k] = fma(a[k], b, c);
   }
-  double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    long long c1 = clock64(), t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    clk[0] = c1 - c0;
+    clk[1] = t1 - t0;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s += a[k];
   if (s == 12345.678) out[0] = s;  // keeps the chains alive
 }
 
@@ -69,24 +125,43 @@ int pp_prof_select(int kind) {
   using namespace pp;
   if (kind < 0 || kind >= PP_K_COUNT) return -1;
   cudaDeviceSynchronize();
-  g_kind = kind;
-  g_used = 0;
-  g_timed = 0;
-  for (int k = 0; k < PP_K_COUNT; ++k) g_launch[k] = 0;
+  reset_all();
+  g_primary = kind;
+  if (kind != PP_K_NONE) g_cls[kind].on = true;
+  return 0;
+}
+
+int pp_prof_sample(int stride) {
+  if (stride < 1) return -1;
+  pp::g_stride = stride;
+  return 0;
+}
+
+int pp_prof_also(int kind) {
+  using namespace pp;
+  if (kind <= PP_K_NONE || kind >= PP_K_COUNT) return -1;
+  g_cls[kind].on = true;
+  return 0;
+}
+
+int pp_prof_read_class(int kind, int64_t* launches, double* total_ms, double* bytes) {
+  using namespace pp;
+  if (kind < 0 || kind >= PP_K_COUNT) return -1;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -6;
+  const ClassTiming& c = g_cls[kind];
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < c.used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]) == cudaSuccess) tot += ms;
+  }
+  if (launches) *launches = c.timed;
+  if (total_ms) *total_ms = tot;
+  if (bytes) *bytes = c.bytes;
   return 0;
 }
 
 int pp_prof_read(int64_t* launches, double* total_ms) {
-  using namespace pp;
-  if (cudaDeviceSynchronize() != cudaSuccess) return -6;
-  double tot = 0.0;
-  for (size_t i = 0; i + 1 < g_used; i += 2) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]) == cudaSuccess) tot += ms;
-  }
-  if (launches) *launches = g_timed;
-  if (total_ms) *total_ms = tot;
-  return 0;
+  return pp_prof_read_class(pp::g_primary, launches, total_ms, nullptr);
 }
 
 int pp_prof_counts(int64_t* counts) {
@@ -96,32 +171,53 @@ int pp_prof_counts(int64_t* counts) {
   return 0;
 }
 
-int pp_measure_fp64_peak(int device, double* tflops) {
+int pp_measure_fp64_peak_clock(int device, double* tflops, double* sm_mhz) {
   using namespace pp;
   if (!tflops) return -1;
   if (cudaSetDevice(device) != cudaSuccess) return -6;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   double* out = nullptr;
+  long long* clk = nullptr;
   if (cudaMalloc(&out, sizeof(double)) != cudaSuccess) return -6;
-  const int threads = 256, blocks = sms * 8, iters = 2048;
-  k_fma_probe<<<blocks, threads>>>(out, 16);  // warm-up
+  if (cudaMalloc(&clk, 2 * sizeof(long long)) != cudaSuccess) {
+    cudaFree(out);
+    return -6;
+  }
+  const int threads = 256, blocks = sms * 8, iters = 1536;
+  k_fma_probe<<<blocks, threads>>>(out, clk, 64);  // warm-up
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  cudaEventRecord(a);
-  k_fma_probe<<<blocks, threads>>>(out, iters);
-  cudaEventRecord(b);
-  cudaError_t e = cudaEventSynchronize(b);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, a, b);
+  double best = 0.0, best_mhz = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(a);
+    k_fma_probe<<<blocks, threads>>>(out, clk, iters);
+    cudaEventRecord(b);
+    e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    long long hc[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(hc, clk, sizeof(hc), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess || ms <= 0.f) break;
+    const double flops = 2.0 * 16.0 * 8.0 * iters * (double)threads * blocks;
+    const double tf = flops / (ms * 1e-3) / 1e12;
+    if (tf > best) {
+      best = tf;
+      best_mhz = hc[1] > 0 ? 1e3 * (double)hc[0] / (double)hc[1] : 0.0;
+    }
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(out);
-  if (e != cudaSuccess || ms <= 0.f) return -6;
-  double flops = 2.0 * 8.0 * 16.0 * iters * (double)threads * blocks;
-  *tflops = flops / (ms * 1e-3) / 1e12;
+  cudaFree(clk);
+  if (e != cudaSuccess || best <= 0.0) return -6;
+  *tflops = best;
+  if (sm_mhz) *sm_mhz = best_mhz;
   return 0;
 }
+
+int pp_measure_fp64_peak(int device, double* tflops) { return pp_measure_fp64_peak_clock(device, tflops, nullptr); }
 
 }  // extern "C"

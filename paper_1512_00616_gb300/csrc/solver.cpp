@@ -101,17 +101,27 @@ int copy(pp_ctx* ctx, int64_t n, S* y, const S* x) {
 // enqueued past convergence is simply not used (its column is beyond ncols).
 template <class S>
 int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const S* b, S* x, double rtol,
-          double atol, int maxit, int* iters, double* res_out, bool flexible = false) {
+          double atol, int maxit, int* iters, double* res_out, bool flexible = false, bool warm = false) {
   const int64_t n = K.n;
   const int m = K.m;
   double* d_h1 = K.d_h;
   double* d_h2 = K.d_h + (m + 2);
   double* d_nrm = K.d_h + 2 * (m + 2);
   const bool flex = flexible && K.Z && prec;
-  PP_CK(cudaMemsetAsync(x, 0, sizeof(S) * n, ctx->stream));
-  PP_TRY(copy<S>(ctx, n, K.r, b));
-  int total = 0;
   bool first = true;
+  if (warm) {
+    // initial guess in x: the tolerance stays relative to |b| (set here), the first cycle
+    // starts from r = b - A x
+    PP_CK(launch_dot<S>(n, b, b, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
+    PP_CK(launch_gmres_init(d_nrm, rtol, atol, 1, m, K.d_g, K.d_stat, ctx->stream));
+    PP_TRY(A(x, K.w));
+    PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
+    first = false;
+  } else {
+    PP_CK(cudaMemsetAsync(x, 0, sizeof(S) * n, ctx->stream));
+    PP_TRY(copy<S>(ctx, n, K.r, b));
+  }
+  int total = 0;
   double res = 0.0;
   int status = PP_ENOCONV;
   for (;;) {
@@ -227,7 +237,7 @@ int stage_solve32(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int tra
 // Stage solve (M - c J) x = b or its transpose.  exact = false (primal Newton steps)
 // may be inexact; exact = true (tangent / adjoint) must reach rtol on the FP64 operator.
 int stage_solve(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans, const double* b, double* x,
-                double rtol, double atol, int* iters, bool exact) {
+                double rtol, double atol, int* iters, bool exact, double* ywarm = nullptr, bool use_warm = false) {
   const DevMesh& m = mesh->dev;
   const int64_t n = ctx->ws_nu;
   if (ctx->cfg.precision == PP_PREC_MIXED) {
@@ -271,8 +281,12 @@ int stage_solve(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans
       PP_CK(launch_stream_rows<double>(m, ctx->tb, ctx->tb.nb, 3, Bf, 0.0, 1.0, in, out, ctx->stream));
       return PP_OK;
     };
-    int st = gmres<double>(ctx, ctx->kin, A, Op(), b, yv, rtol, atol, ctx->cfg.gmres_maxit, iters, nullptr);
+    // warm start (linear sweeps): the same stage's y of the previous step is the initial guess
+    if (ywarm && use_warm) PP_TRY(copy(ctx, n, yv, ywarm));
+    int st = gmres<double>(ctx, ctx->kin, A, Op(), b, yv, rtol, atol, ctx->cfg.gmres_maxit, iters, nullptr, false,
+                           ywarm && use_warm);
     if (st != PP_OK && st != PP_ENOCONV) return st;
+    if (ywarm) PP_TRY(copy(ctx, n, ywarm, yv));
     if (!trans) PP_CK(launch_block_apply<double>(m, ctx->tb.nb, sv.Ainv, yv, x, 0, ctx->stream));
     else if (sv.AinvT) PP_CK(launch_block_apply<double>(m, ctx->tb.nb, sv.AinvT, yv, x, 0, ctx->stream));
     else PP_CK(launch_block_apply<double>(m, ctx->tb.nb, sv.Ainv, yv, x, 1, ctx->stream));
@@ -581,7 +595,8 @@ int tangent_sweep(pp_ctx* ctx, const double* v, double* out) {
       }
       PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.J, 0.0, dt, win, rhs, 0, ctx->stream));
       int gits = 0;
-      PP_TRY(stage_solve(ctx, mesh, sv, 0, rhs, dk[i], ctx->cfg.lin_rtol, 0.0, &gits, true));
+      PP_TRY(stage_solve(ctx, mesh, sv, 0, rhs, dk[i], ctx->cfg.lin_rtol, 0.0, &gits, true, work_vec(ctx, 27 + i),
+                         step > 0));
       ctx->last_gmres_tangent += gits;
     }
     PP_TRY(lincomb(ctx, n, du, {1.0, ctx->b[0], ctx->b[1], ctx->b[2]}, {du, dk[0], dk[1], dk[2]}));
@@ -641,7 +656,8 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
                          {rhs, g[0], g[1], g[2]}));
       }
       int gits = 0;
-      PP_TRY(stage_solve(ctx, mesh, sv, 1, rhs, kap, ctx->cfg.lin_rtol, 0.0, &gits, true));
+      PP_TRY(stage_solve(ctx, mesh, sv, 1, rhs, kap, ctx->cfg.lin_rtol, 0.0, &gits, true, work_vec(ctx, 27 + i),
+                         step < Nt - 1));
       ctx->last_gmres_adjoint += gits;
       if (sv.JT) PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.JT, 0.0, dt, kap, y[i], 0, ctx->stream));
       else PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.J, 0.0, dt, kap, y[i], 1, ctx->stream));
@@ -793,6 +809,13 @@ int shoot_nk(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const
   // outer-level scratch: the last three outer Krylov vectors are free between GMRES calls
   Krylov& K = ctx->kout;
   double* uN = K.r;   // reused only outside gmres
+  // nonlinear preconditioning (Sec. 6.1): m steps of Algorithm fixedpt, u0 <- u^(Nt)(u0)
+  for (int it = 0; it < ctx->cfg.nk_fixed_point_pre; ++it) {
+    PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0_out, Nt, nullptr, uN, nullptr));
+    st.primal_sweeps++;
+    st.stage_newton_iters += ctx->last_newton_iters;
+    PP_TRY(copy(ctx, n, u0_out, uN));
+  }
   int status = PP_ENOCONV;
   for (int it = 0; it <= ctx->cfg.nk_max_newton; ++it) {
     PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0_out, Nt, nullptr, uN, qoi));
@@ -874,6 +897,297 @@ int periodic_adjoint(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_m
     stats->seconds = now_s() - t_start;
   }
   if (gs == PP_ENOCONV) return set_error(ctx, PP_ENOCONV, "periodic adjoint GMRES hit adj_maxit");
+  return PP_OK;
+}
+
+// --------------------------------------------------------------------------- fixed points
+// Algorithm fixedpt: u0 <- u^(Nt)(u0) until ||u^(Nt)(u0) - u0||_2 <= tol (Eq. fixedpt).  On
+// return the stored linearization is that of the returned u0.
+int shoot_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0_guess,
+                      int Nt, double tol, int maxit, double* u0_out, double* qoi, pp_shoot_stats* stats) {
+  const double t_start = now_s();
+  PP_TRY(ensure_store(ctx, mesh, Nt));
+  const int64_t n = ctx->ws_nu;
+  pp_shoot_stats st{};
+  PP_TRY(copy(ctx, n, u0_out, u0_guess));
+  double* uN = ctx->kout.r;
+  double* R = work_vec(ctx, 24);
+  int status = PP_ENOCONV;
+  for (int it = 0; it <= maxit; ++it) {
+    PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0_out, Nt, nullptr, uN, qoi));
+    st.primal_sweeps++;
+    st.stage_newton_iters += ctx->last_newton_iters;
+    PP_TRY(lincomb(ctx, n, R, {1.0, -1.0}, {uN, u0_out}));
+    double rn;
+    PP_TRY(host_norm(ctx, n, R, &rn));
+    if (it < 64) st.residual[it] = rn;
+    st.newton_iters = it;
+    if (!std::isfinite(rn)) return set_error(ctx, PP_ENAN, "fixed-point iteration: non-finite residual");
+    if (rn <= tol) {
+      status = PP_OK;
+      break;
+    }
+    if (it == maxit) break;
+    PP_TRY(copy(ctx, n, u0_out, uN));
+  }
+  st.seconds = now_s() - t_start;
+  if (stats) *stats = st;
+  if (status != PP_OK) return set_error(ctx, PP_ENOCONV, "fixed-point iteration did not reach the tolerance");
+  return PP_OK;
+}
+
+// The periodic adjoint condition (Eq. fixedpt-dual; dF/du^(Nt) = 0 for stage-only QoIs) by
+// fixed-point iteration x <- lambda^(0)(x) from x = 0, then the gradient of Algorithm grad
+// with the converged multipliers.  Iterations and the final residual go to stats.
+int periodic_adjoint_fixed_point(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0,
+                                 int Nt, const double* weights, double tol, int maxit, double* F, double* dFdmu,
+                                 double* lam_Nt, pp_adj_stats* stats) {
+  const double t_start = now_s();
+  if (u0) PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0, Nt, nullptr, nullptr, nullptr));
+  if (!ctx->lin_valid) return set_error(ctx, PP_ESTATE, "periodic adjoint: no stored primal sweep");
+  const int64_t n = ctx->ws_nu;
+  double* x = ctx->kout.V;
+  double* y = ctx->kout.w;
+  double* r = ctx->kout.t;
+  PP_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+  double res = 0.0;
+  int its = 0, status = PP_ENOCONV;
+  for (;; ++its) {
+    PP_TRY(adjoint_sweep(ctx, x, weights, y, nullptr));
+    PP_TRY(lincomb(ctx, n, r, {1.0, -1.0}, {y, x}));
+    PP_TRY(host_norm(ctx, n, r, &res));
+    if (!std::isfinite(res)) return set_error(ctx, PP_ENAN, "dual fixed point: non-finite residual");
+    if (res <= tol) {
+      status = PP_OK;
+      break;
+    }
+    if (its >= maxit) break;
+    PP_TRY(copy(ctx, n, x, y));
+  }
+  // gradient and multipliers of the converged final condition
+  PP_TRY(adjoint_sweep(ctx, x, weights, y, dFdmu));
+  if (lam_Nt) PP_TRY(copy(ctx, n, lam_Nt, x));
+  if (F) *F = weights[0] * ctx->lin_W + weights[1] * ctx->lin_Jx;
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  if (stats) {
+    stats->krylov_iters = its + 1;
+    stats->residual = res;
+    stats->seconds = now_s() - t_start;
+  }
+  if (status != PP_OK) return set_error(ctx, PP_ENOCONV, "dual fixed point did not reach the tolerance");
+  return PP_OK;
+}
+
+// --------------------------------------------------------------------------- multi-QoI adjoint
+namespace {
+
+// Least squares min ||E - H Y||_F for the (r x c) block Hessenberg H (row-major, r > c) and
+// E (r x s) by Householder QR on the host; returns Y (c x s) and the residual norms of the
+// s columns.
+void small_lsq(int r, int c, int s, std::vector<double> H, std::vector<double> E, std::vector<double>& Y,
+               std::vector<double>& res) {
+  for (int k = 0; k < c; ++k) {
+    double nrm = 0.0;
+    for (int i = k; i < r; ++i) nrm += H[(size_t)i * c + k] * H[(size_t)i * c + k];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) continue;
+    const double alpha = H[(size_t)k * c + k] >= 0.0 ? -nrm : nrm;
+    std::vector<double> v(r, 0.0);
+    for (int i = k; i < r; ++i) v[i] = H[(size_t)i * c + k];
+    v[k] -= alpha;
+    double vv = 0.0;
+    for (int i = k; i < r; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    for (int j = k; j < c; ++j) {
+      double d = 0.0;
+      for (int i = k; i < r; ++i) d += v[i] * H[(size_t)i * c + j];
+      d *= 2.0 / vv;
+      for (int i = k; i < r; ++i) H[(size_t)i * c + j] -= d * v[i];
+    }
+    for (int j = 0; j < s; ++j) {
+      double d = 0.0;
+      for (int i = k; i < r; ++i) d += v[i] * E[(size_t)i * s + j];
+      d *= 2.0 / vv;
+      for (int i = k; i < r; ++i) E[(size_t)i * s + j] -= d * v[i];
+    }
+  }
+  Y.assign((size_t)c * s, 0.0);
+  for (int j = 0; j < s; ++j) {
+    for (int k = c - 1; k >= 0; --k) {
+      double acc = E[(size_t)k * s + j];
+      for (int l = k + 1; l < c; ++l) acc -= H[(size_t)k * c + l] * Y[(size_t)l * s + j];
+      const double d = H[(size_t)k * c + k];
+      Y[(size_t)k * s + j] = d != 0.0 ? acc / d : 0.0;
+    }
+  }
+  res.assign(s, 0.0);
+  for (int j = 0; j < s; ++j) {
+    double acc = 0.0;
+    for (int i = c; i < r; ++i) acc += E[(size_t)i * s + j] * E[(size_t)i * s + j];
+    res[j] = std::sqrt(acc);
+  }
+}
+
+}  // namespace
+
+// The periodic adjoint problems of several QoIs, (Phi^T - I) x_q = -d_q with d_q =
+// lambda^(0)(0) under weights q, by one restarted block GMRES: the operator is the same for
+// every QoI (Sec. 4), so all right-hand sides share one block Krylov space.  The basis grows
+// by the s images A v of the newest block, each orthogonalized against every earlier basis
+// vector (two classical Gram-Schmidt passes), so A V_m = V_(m+1) H with H block upper
+// Hessenberg; the s least-squares problems min ||E_1 S - H Y|| share H.  Then per QoI the
+// final sweep with the QoI terms gives dF/dmu (Algorithm grad).
+int periodic_adjoint_multi(pp_ctx* ctx, const pp_mesh* mesh, const double* mu, int n_mu, const double* u0, int Nt,
+                           int n_qoi, const double* weights, double* F, double* dFdmu, double* lam_Nt,
+                           pp_adj_stats* stats) {
+  const double t_start = now_s();
+  if (u0) PP_TRY(primal_sweep(ctx, mesh, mu, n_mu, u0, Nt, nullptr, nullptr, nullptr));
+  if (!ctx->lin_valid) return set_error(ctx, PP_ESTATE, "periodic adjoint: no stored primal sweep");
+  const int s = n_qoi;
+  const int64_t n = ctx->ws_nu;
+  Krylov& K = ctx->kout;
+  const int mb = std::max(1, std::min(K.m, 64) / s - 1);  // block steps per restart: (mb + 1) s <= basis size
+  const int nvec = (mb + 1) * s;
+  if (nvec > K.m + 1) return set_error(ctx, PP_EINVAL, "multi-QoI adjoint: adj_restart too small for the QoI count");
+  double* V = K.V;                          // [(mb+1) s][n] basis (the outer Krylov level's vectors)
+  double* X = nullptr;                      // [s][n] solutions
+  double* Bm = nullptr;                     // [s][n] right-hand sides -d_q
+  if (cudaMalloc(&X, sizeof(double) * (size_t)s * n) != cudaSuccess ||
+      cudaMalloc(&Bm, sizeof(double) * (size_t)s * n) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(X);
+    return set_error(ctx, PP_ENOMEM, "multi-QoI adjoint: allocation failed");
+  }
+  struct Guard {
+    double* a;
+    double* b;
+    ~Guard() {
+      cudaFree(a);
+      cudaFree(b);
+    }
+  } guard{X, Bm};
+  double* w = work_vec(ctx, 24);
+  double* zero = work_vec(ctx, 25);
+  double* d_h = K.d_h;                      // scratch of >= 2 (64 + 2) doubles
+  PP_CK(cudaMemsetAsync(zero, 0, sizeof(double) * n, ctx->stream));
+  PP_CK(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)s * n, ctx->stream));
+  int sweeps = 0;
+  for (int q = 0; q < s; ++q) {
+    PP_TRY(adjoint_sweep(ctx, zero, weights + 2 * q, Bm + (size_t)q * n, nullptr));
+    ++sweeps;
+    PP_TRY(lincomb(ctx, n, Bm + (size_t)q * n, {-1.0}, {Bm + (size_t)q * n}));
+  }
+  // A v = lambda^(0)(v) - v (sensitivity sweep without QoI terms)
+  auto apply = [&](const double* in, double* out) -> int {
+    PP_TRY(adjoint_sweep(ctx, in, nullptr, out, nullptr));
+    ++sweeps;
+    return lincomb(ctx, n, out, {1.0, -1.0}, {out, in});
+  };
+  // orthogonalize w against V[0..k) (two passes); returns the coefficients and |w|
+  std::vector<double> hbuf(66);
+  auto ortho = [&](int k, double* coef, double* nrm) -> int {
+    for (int t = 0; t < k; ++t) coef[t] = 0.0;
+    double n2 = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (k > 0) {
+        PP_CK(launch_mdot<double>(n, V, n, k, w, d_h, ctx->d_partial, ctx->d_counter, ctx->stream));
+        PP_CK(launch_update_norm2<double>(n, V, n, k, d_h, w, d_h + 64, ctx->d_partial, ctx->d_counter, ctx->stream));
+      } else {
+        PP_CK(launch_dot<double>(n, w, w, d_h + 64, ctx->d_partial, ctx->d_counter, ctx->stream));
+      }
+      PP_CK(cudaMemcpyAsync(hbuf.data(), d_h, sizeof(double) * 65, cudaMemcpyDeviceToHost, ctx->stream));
+      PP_CK(cudaStreamSynchronize(ctx->stream));
+      for (int t = 0; t < k; ++t) coef[t] += hbuf[t];
+      n2 = hbuf[64];
+    }
+    *nrm = std::sqrt(std::max(n2, 0.0));
+    return PP_OK;
+  };
+  std::vector<double> res(s, 0.0), Y;
+  int iters = 0, status = PP_ENOCONV;
+  const double tol = ctx->cfg.adj_tol;
+  for (int cycle = 0; cycle < 1000; ++cycle) {
+    // residual block R = B - A X, its QR R = V_1 S
+    std::vector<double> S((size_t)s * s, 0.0), coef(64);
+    for (int q = 0; q < s; ++q) {
+      if (cycle == 0) {
+        PP_TRY(copy(ctx, n, w, Bm + (size_t)q * n));
+      } else {
+        PP_TRY(apply(X + (size_t)q * n, w));
+        PP_TRY(lincomb(ctx, n, w, {1.0, -1.0}, {Bm + (size_t)q * n, w}));
+      }
+      double nr;
+      PP_TRY(ortho(q, coef.data(), &nr));
+      for (int t = 0; t < q; ++t) S[(size_t)t * s + q] = coef[t];
+      S[(size_t)q * s + q] = nr;
+      PP_CK(launch_scale(n, V + (size_t)q * n, nr > 0.0 ? 1.0 / nr : 0.0, w, ctx->stream));
+    }
+    // the true residual norms of this cycle's start
+    bool done = true;
+    for (int q = 0; q < s; ++q) {
+      double r2 = 0.0;
+      for (int t = 0; t <= q; ++t) r2 += S[(size_t)t * s + q] * S[(size_t)t * s + q];
+      res[q] = std::sqrt(r2);
+      if (!(res[q] <= tol)) done = false;
+    }
+    if (done) {
+      status = PP_OK;
+      break;
+    }
+    if (iters >= ctx->cfg.adj_maxit) break;
+    std::vector<double> H((size_t)nvec * (mb * s), 0.0);
+    int cols = 0;
+    for (int j = 0; j < mb && iters < ctx->cfg.adj_maxit; ++j) {
+      for (int i = 0; i < s; ++i) {
+        const int c = j * s + i;   // new column: A applied to basis vector c
+        PP_TRY(apply(V + (size_t)c * n, w));
+        double nr;
+        const int k = c + s;       // vectors present: the first block plus the new ones so far
+        PP_TRY(ortho(k, coef.data(), &nr));
+        for (int t = 0; t < k; ++t) H[(size_t)t * (mb * s) + c] = coef[t];
+        H[(size_t)k * (mb * s) + c] = nr;
+        PP_CK(launch_scale(n, V + (size_t)k * n, nr > 0.0 ? 1.0 / nr : 0.0, w, ctx->stream));
+      }
+      ++iters;
+      cols = (j + 1) * s;
+      const int rows = cols + s;
+      std::vector<double> Hs((size_t)rows * cols), E((size_t)rows * s, 0.0);
+      for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) Hs[(size_t)r * cols + c] = H[(size_t)r * (mb * s) + c];
+      for (int r = 0; r < s; ++r)
+        for (int q = 0; q < s; ++q) E[(size_t)r * s + q] = S[(size_t)r * s + q];
+      small_lsq(rows, cols, s, Hs, E, Y, res);
+      bool conv = true;
+      for (int q = 0; q < s; ++q)
+        if (!(res[q] <= tol)) conv = false;
+      if (conv) break;
+    }
+    // X += V Y
+    for (int q = 0; q < s; ++q)
+      for (int c = 0; c < cols; ++c) {
+        const double yc = Y[(size_t)c * s + q];
+        if (yc != 0.0) PP_TRY(lincomb(ctx, n, X + (size_t)q * n, {1.0, yc}, {X + (size_t)q * n, V + (size_t)c * n}));
+      }
+  }
+  // gradients with the converged multipliers (Algorithm grad), one final sweep per QoI
+  double resmax = 0.0;
+  for (int q = 0; q < s; ++q) {
+    PP_TRY(adjoint_sweep(ctx, X + (size_t)q * n, weights + 2 * q, w, dFdmu + (size_t)q * n_mu));
+    ++sweeps;
+    PP_TRY(lincomb(ctx, n, w, {1.0, -1.0}, {w, X + (size_t)q * n}));
+    double r;
+    PP_TRY(host_norm(ctx, n, w, &r));
+    resmax = std::max(resmax, r);
+    if (lam_Nt) PP_TRY(copy(ctx, n, lam_Nt + (size_t)q * n, X + (size_t)q * n));
+    if (F) F[q] = weights[2 * q] * ctx->lin_W + weights[2 * q + 1] * ctx->lin_Jx;
+  }
+  PP_CK(cudaStreamSynchronize(ctx->stream));
+  if (stats) {
+    stats->krylov_iters = sweeps;
+    stats->residual = resmax;
+    stats->seconds = now_s() - t_start;
+  }
+  if (status != PP_OK) return set_error(ctx, PP_ENOCONV, "multi-QoI adjoint: block GMRES hit adj_maxit");
   return PP_OK;
 }
 

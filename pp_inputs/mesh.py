@@ -8,6 +8,7 @@ Conventions shared by every consumer (they are part of the C-ABI contract):
 * ``ftag``   int32 [nt, 3] tag of local face f = edge (v_f, v_{(f+1)%3}):
   0 interior, 1 wall (airfoil, no-slip), 2 far field.
 """
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -77,21 +78,48 @@ def _wall_points(n_theta, thickness, clustering):
     return beta, np.stack([xw, yw], 1)
 
 
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed, counter):
+    """Output number `counter` of the SplitMix64 generator started at `seed` (Steele, Lea and
+    Flood, 2014): state = seed + (counter + 1) * 0x9E3779B97F4A7C15, then the published
+    xor-shift-multiply finalizer.  Counter-based, so every consumer draws the same numbers."""
+    z = (seed + (counter + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def uniform_pm1(seed, counter):
+    """A double in [-1, 1) from the top 53 bits of splitmix64(seed, counter)."""
+    return -1.0 + 2.0 * ((splitmix64(seed, counter) >> 11) * (1.0 / 9007199254740992.0))
+
+
 def ogrid(n_theta, n_r, seed=0, r_far=10.0, jitter=0.1, thickness=0.12, clustering="arclength"):
-    """O-grid of 2*n_theta*n_r triangles around a symmetric 4-digit airfoil."""
+    """O-grid of 2*n_theta*n_r triangles around a symmetric 4-digit airfoil.  Interior vertex
+    (k, j) moves by jitter * h * (u1, u2), h its distance to the nearest of its four grid
+    neighbours at that moment (rings j = 1 .. n_r - 1 in order, k inner), u1, u2 the next two
+    numbers of uniform_pm1(seed, .)."""
     beta, wall = _wall_points(n_theta, thickness, clustering)
     far = np.stack([0.5 + r_far * np.cos(beta), r_far * np.sin(beta)], 1)
     q = 1.0 + 4.0 / n_r
     s = (q ** np.arange(n_r + 1) - 1.0) / (q ** n_r - 1.0)
     P = wall[:, None, :] + s[None, :, None] * (far - wall)[:, None, :]  # [n_theta, n_r+1, 2]
 
-    rng = np.random.Generator(np.random.PCG64(seed))
     if n_r >= 2 and jitter > 0:
+        draw = 0
         for j in range(1, n_r):
             for k in range(n_theta):
-                nbrs = [P[(k + 1) % n_theta, j], P[(k - 1) % n_theta, j], P[k, j + 1], P[k, j - 1]]
-                h = min(np.linalg.norm(P[k, j] - x) for x in nbrs)
-                P[k, j] = P[k, j] + jitter * h * rng.uniform(-1.0, 1.0, 2)
+                x0, y0 = float(P[k, j, 0]), float(P[k, j, 1])
+                h = None
+                for kk, jj in (((k + 1) % n_theta, j), ((k - 1) % n_theta, j), (k, j + 1), (k, j - 1)):
+                    dx, dy = x0 - float(P[kk, jj, 0]), y0 - float(P[kk, jj, 1])
+                    d = math.sqrt(dx * dx + dy * dy)
+                    h = d if h is None or d < h else h
+                P[k, j, 0] = x0 + jitter * h * uniform_pm1(seed, draw)
+                P[k, j, 1] = y0 + jitter * h * uniform_pm1(seed, draw + 1)
+                draw += 2
 
     vid = np.arange(n_theta * (n_r + 1)).reshape(n_theta, n_r + 1)
     ring = np.tile(np.arange(n_r + 1), n_theta)

@@ -56,6 +56,27 @@ def test_jacobi_eigensolver_and_pod():
     assert np.max(np.abs(rec - snaps)) <= 1e-9 * np.max(np.abs(snaps))
 
 
+@pytest.mark.parametrize("n", [257, 512])
+def test_jacobi_eigensolver_multi_block(n):
+    """n > 256 (the 512-snapshot Gram matrix of the configured POD): the multi-CTA sweeps
+    against LAPACK's symmetric eigensolver, with a clustered spectrum like a Gram matrix."""
+    from paper_1512_00616_gb300 import api as A
+    rng = np.random.default_rng(n)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.exp(-np.linspace(0.0, 20.0, n)) * rng.uniform(0.5, 1.5, n)   # decaying, like POD
+    S = (Q * lam) @ Q.T
+    S = 0.5 * (S + S.T)
+    G = torch.tensor(S, dtype=torch.float64, device="cuda")
+    V = torch.zeros_like(G)
+    w = torch.zeros(n, dtype=torch.float64, device="cuda")
+    A.pp_syevj_f64(G, V, w)
+    wn, Vn = w.cpu().numpy(), V.cpu().numpy()
+    ref = np.linalg.eigvalsh(S)
+    assert np.max(np.abs(np.sort(wn) - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.linalg.norm(S @ Vn - Vn * wn) <= 1e-11 * np.linalg.norm(S)
+    assert np.max(np.abs(Vn.T @ Vn - np.eye(n))) <= 1e-11
+
+
 def test_learned_warm_start_beats_cold_start():
     from paper_1512_00616_gb300.warmstart import experiment
     r = experiment("tiny", n_train=24, n_test=3, tol=1e-8, epochs=4000)

