@@ -328,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
                 counts=counts, e2e=e2e)
 
 
-# kernel classes timed by the bench: (folded stage operator, Gram-Schmidt passes of an Arnoldi step)
+# kernel classes timed by the bench: (folded stage operator, fused Arnoldi step)
 KERNELS = {"fp64": ("stage_op", "arnoldi"), "mixed": ("stage_op32", "arnoldi32")}
 PROF_STRIDE = 8   # one launch (one Arnoldi step) in 8 is bracketed by CUDA events
 
@@ -347,12 +347,13 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c, sustained):
     t = ms / launches * 1e-3
     hbm = peaks["hbm_gbs"]
     if kernel.startswith("arnoldi"):
-        # bytes of one classical Gram-Schmidt pass over the basis, counted per Arnoldi step
-        # at launch (2k + 3) n words; 3 launches per step
+        # bytes of one fused Arnoldi step over k basis vectors of length n, counted at launch:
+        # (2k + 5) n words (two Gram-Schmidt passes and the scaling of the new basis vector;
+        # a selective second update is not counted); one cooperative launch per step
         ach = counted / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": "k_cgs<KB,%s> x3 (one Arnoldi orthogonalization step)"
-                % ("double" if kernel == "arnoldi" else "float"),
+                "traffic": None, "kernel": "k_arnoldi<KB,%s> (one fused Arnoldi step: Gram-Schmidt "
+                "passes, Givens update, scaling)" % ("double" if kernel == "arnoldi" else "float"),
                 "launches": launches, "avg_us": t * 1e6, "algorithmic_bytes_per_launch": counted / launches,
                 "note": "basis of one stage solve (<= 41 x N_u words) is L2-resident: a low fraction means "
                         "latency-bound grid reductions, not HBM"}

@@ -38,6 +38,7 @@ struct KrylovT {
   S* Z = nullptr;        // [m][n] or null
   double* d_h = nullptr; // device: h1 [m+2] | h2 [m+2] | norm2 | y | H [(m+1) m] | cs | sn | g | stat [8]
   double* h_h = nullptr; // pinned ring of stat copies [kRing][8]
+  double* h_h_dev = nullptr; // device alias of h_h (null: copied by cudaMemcpyAsync)
   double* d_y = nullptr; // [m+1]
   double* d_H = nullptr;
   double* d_cs = nullptr;
@@ -75,6 +76,10 @@ struct pp_ctx {
   double* d_scalar = nullptr;  // [64]
   double* h_scalar = nullptr;  // pinned [64]
   int* d_status = nullptr;
+  double* d_arn = nullptr;     // fused Arnoldi step: CTA partials
+  unsigned* d_arn_bar = nullptr;  // fused Arnoldi step: arrival count, release epoch, error word
+  double* d_gterm = nullptr;   // adjoint-sweep gradient terms, 9 per stage [3 * Nt][9]
+  size_t gterm_cap = 0;        // capacity in stages
 
   // per-mesh-size workspace
   int64_t ws_nu = 0;

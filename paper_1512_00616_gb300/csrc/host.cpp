@@ -267,7 +267,7 @@ static void free_krylov(KrylovT<S>& k) {
   cudaFree(k.d_h);
   if (k.h_h) cudaFreeHost(k.h_h);
   k.V = k.Z = nullptr;
-  k.d_h = k.h_h = nullptr;
+  k.d_h = k.h_h = k.h_h_dev = nullptr;
 }
 
 template <class S>
@@ -284,6 +284,10 @@ static int alloc_krylov(pp_ctx* ctx, KrylovT<S>& k, int m, int64_t n, bool flexi
   PP_CK(cudaMalloc(&k.d_h, sizeof(double) * nh));
   PP_CK(cudaMemset(k.d_h, 0, sizeof(double) * nh));
   PP_CK(cudaMallocHost(&k.h_h, sizeof(double) * 8 * kRing + 64));
+  // the fused Arnoldi step writes the convergence record straight into the ring
+  void* dev_alias = nullptr;
+  k.h_h_dev = cudaHostGetDevicePointer(&dev_alias, k.h_h, 0) == cudaSuccess ? (double*)dev_alias : nullptr;
+  cudaGetLastError();
   k.d_y = k.d_h + 2 * (m + 2) + 4;
   k.d_H = k.d_y + (m + 2);
   k.d_cs = k.d_H + (size_t)(m + 1) * m;
@@ -542,10 +546,13 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
       cudaMalloc(&ctx->d_counter, sizeof(unsigned) * 4) != cudaSuccess ||
       cudaMalloc(&ctx->d_scalar, sizeof(double) * 64) != cudaSuccess ||
       cudaMalloc(&ctx->d_status, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc(&ctx->d_arn, sizeof(double) * arnoldi_partial_words()) != cudaSuccess ||
+      cudaMalloc(&ctx->d_arn_bar, sizeof(unsigned) * arnoldi_barrier_words()) != cudaSuccess ||
       cudaMallocHost(&ctx->h_scalar, sizeof(double) * 64) != cudaSuccess)
     return fail(PP_ENOMEM);
   if (cudaMemset(ctx->d_counter, 0, sizeof(unsigned) * 4) != cudaSuccess ||
-      cudaMemset(ctx->d_status, 0, sizeof(int) * 4) != cudaSuccess)
+      cudaMemset(ctx->d_status, 0, sizeof(int) * 4) != cudaSuccess ||
+      cudaMemset(ctx->d_arn_bar, 0, sizeof(unsigned) * arnoldi_barrier_words()) != cudaSuccess)
     return fail(PP_ECUDA);
   *out = ctx;
   return PP_OK;
@@ -560,6 +567,9 @@ int pp_destroy(pp_ctx* ctx) {
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_scalar);
   cudaFree(ctx->d_status);
+  cudaFree(ctx->d_gterm);
+  cudaFree(ctx->d_arn);
+  cudaFree(ctx->d_arn_bar);
   if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
   cudaFree(ctx->d_J);
   cudaFree(ctx->d_Ainv);

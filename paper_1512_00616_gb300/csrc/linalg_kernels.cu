@@ -785,6 +785,267 @@ __global__ void __launch_bounds__(CGS_T, 1) k_cgs(CgsArgs<S> a) {
   if (mode == 2 && a.gv.H) givens_update(a.gv, out[0]);
 }
 
+// ------------------------------------------------------------------ fused Arnoldi step
+// One cooperative launch per Arnoldi step (replaces the three Gram-Schmidt launches, the
+// host copy of the convergence record and the scaling launch).  Every CTA stays resident
+// (cooperative launch, one CTA per SM at most) and the passes are separated by grid
+// barriers; after each barrier EVERY CTA sums the CTA partials itself, in one fixed order
+// (warp w sums outputs w, w + 8, ...; lanes stride over the CTAs, then a xor butterfly),
+// so all CTAs hold bitwise the same coefficients and no CTA waits for a last-arriving one.
+// Passes (k <= KB basis vectors in registers):
+//   1. h1 = V^T w and |w|^2
+//   2. w -= V h1, then h2 = V^T w if more than half of |w|^2 cancelled, else |w|^2
+//   3. (only if needed) w -= V h2, |w|^2
+// then v_k = w / |w| in every CTA, and CTA 0 applies the Givens update and writes the
+// convergence record to the pinned host ring.  Barrier waits are bounded (about a second);
+// an expired wait sets the error word, the convergence flag 8 and ends the kernel.
+constexpr unsigned long long kArnBarrierNs = 1000000000ull;
+constexpr int ARN_LD = CGS_MAXKB + 2;       // partial rows (outputs) per exchange
+constexpr int ARN_NB = CGS_MAX_BLOCKS;      // partial columns (CTAs)
+// barrier words, each on its own 128-byte line: arrival count (u32), release epoch (u64),
+// error word (u32)
+constexpr int ARN_BAR_COUNT = 0, ARN_BAR_EPOCH = 32, ARN_BAR_ERROR = 64, ARN_BAR_WORDS = 96;
+
+template <class S>
+struct ArnArgs {
+  int64_t n;
+  const S* V;
+  int64_t ldv;
+  int k;
+  S* w;                 // A v_{k-1} on entry; w - V (h1 + h2) on exit
+  S* vnext;             // V column k on exit: w / |w|
+  double* h1;
+  double* h2;
+  double* nrm;
+  double* partial;      // [2][ARN_LD][ARN_NB], alternating between exchanges
+  unsigned* bar;        // ARN_BAR_WORDS words (see above), zero before the first launch
+  double* host_stat;    // device alias of the pinned ring slot (or null)
+  GivensArgs gv;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier number `target` of this launch (epochs continue across launches).  Thread 0
+// of each CTA arrives with an acquire-release add (its CTA's partials, ordered by the
+// preceding __syncthreads, become visible with it); the last arrival resets the count and
+// publishes the epoch with a release store; the others poll the epoch with acquire loads,
+// for at most kArnBarrierNs.
+__device__ __forceinline__ bool arn_grid_barrier(unsigned* bar, unsigned long long target) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    unsigned long long* epoch = reinterpret_cast<unsigned long long*>(bar + ARN_BAR_EPOCH);
+    const unsigned prev = atom_add_acq_rel_u32(bar + ARN_BAR_COUNT, 1u);
+    if (prev == gridDim.x - 1u) {
+      st_relaxed_u32(bar + ARN_BAR_COUNT, 0u);
+      st_release_u64(epoch, target);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned it = 0;
+      while (ld_acquire_u64(epoch) < target) {
+        if ((++it & 255u) == 0u && global_ns() - t0 > kArnBarrierNs) {
+          atomicExch(bar + ARN_BAR_ERROR, 1u);
+          good = 0;
+          break;
+        }
+      }
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// CTA partials bp[0..nk) -> column blockIdx.x of the region, grid barrier, then every CTA
+// forms out[j] = sum_b region[j][b] (out in shared memory), in the same order everywhere.
+__device__ __forceinline__ bool arn_exchange(int nk, const double* bp, double* region, unsigned* bar,
+                                             unsigned long long target, double* out) {
+  for (int t = threadIdx.x; t < nk; t += CGS_T) region[(size_t)t * ARN_NB + blockIdx.x] = bp[t];
+  if (!arn_grid_barrier(bar, target)) return false;
+  constexpr int NW = CGS_T / 32;
+  constexpr int R = (ARN_NB + 31) / 32;
+  constexpr int Q = (ARN_LD + NW - 1) / NW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nb = gridDim.x;
+  double s[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = warp + NW * q;
+    double acc = 0.0;
+    if (j < nk) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int b = lane + 32 * r;
+        if (b < nb) acc += __ldcg(region + (size_t)j * ARN_NB + b);
+      }
+    }
+    s[q] = acc;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (warp + NW * q < nk) out[warp + NW * q] = s[q];
+  }
+  __syncthreads();
+  return true;
+}
+
+template <int KB, class S>
+__global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
+  constexpr int K2 = Pow2Up<KB>::value;
+  __shared__ double bp[CGS_MAXK + 1];
+  __shared__ double red[CGS_MAXKB + 1];  // result of the last exchange
+  __shared__ double hA[KB], hB[KB];      // h1, h2 (zero beyond k)
+  __shared__ int s_need;
+  const int k = a.k;
+  const int64_t n = a.n;
+  const S* __restrict__ V = a.V;
+  S* __restrict__ w = a.w;
+  const int64_t ldv = a.ldv;
+  const int64_t stride = (int64_t)gridDim.x * CGS_T;
+  const int64_t i0 = (int64_t)blockIdx.x * CGS_T + threadIdx.x;
+  double* region0 = a.partial;
+  double* region1 = a.partial + (size_t)ARN_LD * ARN_NB;
+  // epoch before this launch's first barrier (stable: it only moves inside a barrier,
+  // which no CTA passes before every CTA has read it here)
+  __shared__ unsigned long long s_epoch;
+  if (threadIdx.x == 0)
+    s_epoch = ld_acquire_u64(reinterpret_cast<const unsigned long long*>(a.bar + ARN_BAR_EPOCH));
+  __syncthreads();
+  const unsigned long long e0 = s_epoch;
+  bool ok;
+  // pass 1: h1 = V^T w, |w|^2
+  {
+    S acc[K2], accs[1] = {S(0)};
+#pragma unroll
+    for (int t = 0; t < K2; ++t) acc[t] = S(0);
+    for (int64_t i = i0; i < n; i += stride) {
+      S v[KB];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
+      const S s = w[i];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) acc[t] += v[t] * s;
+      accs[0] += s * s;
+    }
+    cta_reduce<K2, S>(acc, k, bp, 0);
+    cta_reduce<1, S>(accs, 1, bp, k);
+  }
+  ok = arn_exchange(k + 1, bp, region0, a.bar, e0 + 1, red);
+  if (ok) {
+    if (threadIdx.x < 32) {
+      double hh;
+      const bool nd = reorth_needed_warp0(red, red[k], k, hh);
+      if (threadIdx.x == 0) s_need = nd ? 1 : 0;
+    }
+    for (int t = threadIdx.x; t < KB; t += CGS_T) {
+      hA[t] = t < k ? red[t] : 0.0;
+      hB[t] = 0.0;
+    }
+    __syncthreads();
+    const bool need = s_need != 0;
+    // pass 2: w -= V h1, then V^T w (second pass) or |w|^2
+    {
+      S acc[K2];
+#pragma unroll
+      for (int t = 0; t < K2; ++t) acc[t] = S(0);
+      for (int64_t i = i0; i < n; i += stride) {
+        S v[KB];
+#pragma unroll
+        for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
+        S s = w[i];
+#pragma unroll
+        for (int t = 0; t < KB; ++t) s -= S(hA[t]) * v[t];
+        w[i] = s;
+        if (need) {
+#pragma unroll
+          for (int t = 0; t < KB; ++t) acc[t] += v[t] * s;
+        } else {
+          acc[0] += s * s;
+        }
+      }
+      if (need) cta_reduce<K2, S>(acc, k, bp, 0);
+      else cta_reduce<1, S>(acc, 1, bp, 0);
+    }
+    ok = arn_exchange(need ? k : 1, bp, region1, a.bar, e0 + 2, red);
+    if (ok && need) {
+      for (int t = threadIdx.x; t < k; t += CGS_T) hB[t] = red[t];
+      __syncthreads();
+      // pass 3: w -= V h2, |w|^2
+      S acc[1] = {S(0)};
+      for (int64_t i = i0; i < n; i += stride) {
+        S v[KB];
+#pragma unroll
+        for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
+        S s = w[i];
+#pragma unroll
+        for (int t = 0; t < KB; ++t) s -= S(hB[t]) * v[t];
+        w[i] = s;
+        acc[0] += s * s;
+      }
+      cta_reduce<1, S>(acc, 1, bp, 0);
+      ok = arn_exchange(1, bp, region0, a.bar, e0 + 3, red);
+    }
+  }
+  if (!ok) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.gv.stat[6] = 8.0;
+      if (a.host_stat) {
+        for (int t = 0; t < 8; ++t) a.host_stat[t] = a.gv.stat[t];
+      }
+    }
+    return;
+  }
+  const double nrm2 = red[0];
+  // v_k = w / |w| (the scaling of k_scale_dev with stat[3] = 1 / hn)
+  {
+    const double hn = sqrt(fmax(nrm2, 0.0));
+    const S inv = S(hn > 0.0 ? 1.0 / hn : 0.0);
+    S* __restrict__ vn = a.vnext;
+    for (int64_t i = i0; i < n; i += stride) vn[i] = inv * w[i];
+  }
+  if (blockIdx.x != 0) return;
+  for (int t = threadIdx.x; t < k; t += CGS_T) {
+    a.h1[t] = hA[t];
+    a.h2[t] = hB[t];
+  }
+  if (threadIdx.x == 0) a.nrm[0] = nrm2;
+  __syncthreads();
+  givens_update(a.gv, nrm2);
+  if (threadIdx.x == 0 && a.host_stat) {
+    for (int t = 0; t < 8; ++t) a.host_stat[t] = a.gv.stat[t];
+  }
+}
+
 // out[j] = sum_e per_elem[e*k + j], k <= 8
 __global__ void __launch_bounds__(RED_THREADS)
     k_colsum(int ne, int k, const double* __restrict__ pe, double* out, double* partial, unsigned* counter) {
@@ -1089,6 +1350,61 @@ cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w
 }
 
 template <class S>
+cudaError_t launch_arnoldi_step(int64_t n, const S* V, int64_t ldv, int k, S* w, S* vnext, double* h1, double* h2,
+                                double* nrm, double* arn_partial, unsigned* arn_bar, double* host_stat, int j, int m,
+                                double* H, double* cs, double* sn, double* g, double* stat, cudaStream_t st) {
+  if (k < 1 || k > CGS_MAXKB) return cudaErrorInvalidValue;
+  const int kind = sizeof(S) == 8 ? PP_K_ARNOLDI : PP_K_ARNOLDI32;
+  // algorithmic traffic: V and w read for the projections; V and w read and w written for
+  // the update and norm; w read and v_k written for the scaling
+  prof_add_bytes(kind, (2.0 * k + 5.0) * (double)n * sizeof(S), 1);
+  ProfScope ps(kind, st);
+  ArnArgs<S> a{};
+  a.n = n;
+  a.V = V;
+  a.ldv = ldv;
+  a.k = k;
+  a.w = w;
+  a.vnext = vnext;
+  a.h1 = h1;
+  a.h2 = h2;
+  a.nrm = nrm;
+  a.partial = arn_partial;
+  a.bar = arn_bar;
+  a.host_stat = host_stat;
+  a.gv = GivensArgs{j, m, h1, h2, H, cs, sn, g, stat};
+  // grid <= SM count and one CTA per SM: every CTA is resident, which the cooperative launch
+  // checks (it fails rather than start a grid that could wait on a CTA that never runs)
+  const int grid = cgs_blocks(n);
+  void* args[] = {&a};
+  cudaError_t e = cudaSuccess;
+  switch ((k + 3) / 4) {
+#define PP_ARN(Q)                                                                                   \
+  case Q:                                                                                           \
+    e = cudaLaunchCooperativeKernel((const void*)k_arnoldi<4 * Q, S>, dim3(grid), dim3(CGS_T), args, 0, st); \
+    break;
+    PP_ARN(1)
+    PP_ARN(2)
+    PP_ARN(3)
+    PP_ARN(4)
+    PP_ARN(5)
+    PP_ARN(6)
+    PP_ARN(7)
+    PP_ARN(8)
+    PP_ARN(9)
+    PP_ARN(10)
+#undef PP_ARN
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return e;
+}
+
+size_t arnoldi_partial_words() { return (size_t)2 * ARN_NB * ARN_LD; }
+int arnoldi_barrier_words() { return ARN_BAR_WORDS; }
+int arnoldi_barrier_error_word() { return ARN_BAR_ERROR; }
+
+template <class S>
 cudaError_t launch_dot(int64_t n, const S* x, const S* y, double* out, double* partial, unsigned* counter,
                        cudaStream_t st) {
   return launch_cgs<S>(cgs_args<S>(3, n, x, 0, 1, nullptr, const_cast<S*>(y), out, partial, counter), st);
@@ -1124,6 +1440,9 @@ cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaSt
                                               unsigned*, cudaStream_t);                                             \
   template cudaError_t launch_fold_blocks<S>(const DevMesh&, int, const S*, const S*, double, S*, S*,         \
                                              cudaStream_t);                                                     \
+  template cudaError_t launch_arnoldi_step<S>(int64_t, const S*, int64_t, int, S*, S*, double*, double*, double*,    \
+                                             double*, unsigned*, double*, int, int, double*, double*, double*,      \
+                                             double*, double*, cudaStream_t);                                       \
   template cudaError_t launch_arnoldi_ortho<S>(int64_t, const S*, int64_t, int, S*, double*, double*, double*,  \
                                                  double*, unsigned*, int, int, double*, double*, double*, double*,  \
                                                  double*, cudaStream_t);                                            \

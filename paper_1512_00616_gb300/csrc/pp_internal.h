@@ -184,6 +184,19 @@ cudaError_t launch_update_norm2(int64_t n, const S* V, int64_t ldv, int k, const
 // (classical Gram-Schmidt, a second pass only when more than half of |w|^2 cancels),
 // ending with the Givens update of Hessenberg column j: h1[0..k] <- (V^T w, |w|^2),
 // h2 the second-pass coefficients (zero when skipped), nrm[0] = |w|^2 after.
+// One fused Arnoldi step (cooperative launch, k <= 40): classical Gram-Schmidt with
+// selective reorthogonalization, the Givens update, v_k = w / |w| and the convergence
+// record (stat[0..8)) also written to host_stat (a device-visible pinned slot, or null).
+// arn_partial holds arnoldi_partial_words() doubles; arn_bar arnoldi_barrier_words() zeroed
+// words (arrival count, release epoch, and an error word set when a barrier wait expired).
+template <class S>
+cudaError_t launch_arnoldi_step(int64_t n, const S* V, int64_t ldv, int k, S* w, S* vnext, double* h1, double* h2,
+                                double* nrm, double* arn_partial, unsigned* arn_bar, double* host_stat, int j, int m,
+                                double* H, double* cs, double* sn, double* g, double* stat, cudaStream_t st);
+size_t arnoldi_partial_words();
+int arnoldi_barrier_words();       // size of arn_bar in 32-bit words
+int arnoldi_barrier_error_word();  // index of the error word in arn_bar
+constexpr int kArnoldiFusedMaxK = 40;
 template <class S>
 cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w, double* h1, double* h2,
                                  double* nrm, double* partial, unsigned* counter, int j, int m, double* H, double* cs,

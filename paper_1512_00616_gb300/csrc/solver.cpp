@@ -61,6 +61,12 @@ int check_stream_kernels(pp_ctx* ctx) {
   int flag = 0;
   PP_CK(stream_rows_error(&flag, true));
   if (flag) return set_error(ctx, PP_ECUDA, "block-row kernel: shared-memory pipeline wait expired");
+  unsigned err = 0u;
+  PP_CK(cudaMemcpy(&err, ctx->d_arn_bar + arnoldi_barrier_error_word(), sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (err != 0u) {
+    PP_CK(cudaMemset(ctx->d_arn_bar, 0, sizeof(unsigned) * arnoldi_barrier_words()));
+    return set_error(ctx, PP_ECUDA, "Arnoldi step: grid barrier wait expired");
+  }
   return PP_OK;
 }
 
@@ -140,12 +146,21 @@ int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const
         z = zj;
       }
       PP_TRY(A(z, K.w));
-      PP_CK(launch_arnoldi_ortho<S>(n, K.V, n, j + 1, K.w, d_h1, d_h2, d_nrm, ctx->d_partial, ctx->d_counter, j, m,
-                                    K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
       double* slot = K.h_h + 8 * (j % kRing);
-      PP_CK(cudaMemcpyAsync(slot, K.d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-      PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
-      PP_CK(launch_scale_dev<S>(n, K.V + (size_t)(j + 1) * n, K.d_stat + 3, K.w, ctx->stream));
+      S* vnext = K.V + (size_t)(j + 1) * n;
+      if (j + 1 <= kArnoldiFusedMaxK && K.h_h_dev) {
+        // one cooperative launch: orthogonalization, Givens, scaling, record into the ring
+        PP_CK(launch_arnoldi_step<S>(n, K.V, n, j + 1, K.w, vnext, d_h1, d_h2, d_nrm, ctx->d_arn, ctx->d_arn_bar,
+                                     K.h_h_dev + 8 * (j % kRing), j, m, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat,
+                                     ctx->stream));
+        PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
+      } else {
+        PP_CK(launch_arnoldi_ortho<S>(n, K.V, n, j + 1, K.w, d_h1, d_h2, d_nrm, ctx->d_partial, ctx->d_counter, j,
+                                      m, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
+        PP_CK(cudaMemcpyAsync(slot, K.d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
+        PP_CK(launch_scale_dev<S>(n, vnext, K.d_stat + 3, K.w, ctx->stream));
+      }
       ++total;
       // look one step behind
       const int jl = (j == m - 1) ? j : j - 1;
@@ -154,6 +169,12 @@ int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const
       const double* st = K.h_h + 8 * (jl % kRing);
       flag = st[6];
       res = st[0];
+      if (flag >= 8.0) {
+        PP_CK(cudaStreamSynchronize(ctx->stream));
+        PP_CK(cudaMemsetAsync(ctx->d_arn_bar, 0, sizeof(unsigned) * arnoldi_barrier_words(), ctx->stream));
+        PP_CK(cudaStreamSynchronize(ctx->stream));
+        return set_error(ctx, PP_ECUDA, "GMRES: Arnoldi grid barrier wait expired");
+      }
       if (flag >= 4.0) return set_error(ctx, PP_ENAN, "GMRES: non-finite Arnoldi quantity");
       if (flag > 0.0 || total - (j - jl) >= maxit || j == m - 1) {
         ncols = jl + 1;
@@ -625,6 +646,21 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
   const bool withF = weights != nullptr;
   const double w0 = withF ? weights[0] : 0.0, w1 = withF ? weights[1] : 0.0;
   std::vector<double> grad(n_mu, 0.0);
+  // kappa_i . dr/ds and the two QoI-rate derivatives for the 3 motion seeds of every stage stay
+  // on the device until the sweep ends: one read-back instead of one host sync per stage.
+  const size_t n_st = (size_t)3 * Nt;
+  std::vector<double> ds_host;
+  if (withF && dFdmu) {
+    if (ctx->gterm_cap < n_st) {
+      PP_CK(cudaStreamSynchronize(ctx->stream));
+      cudaFree(ctx->d_gterm);
+      ctx->d_gterm = nullptr;
+      ctx->gterm_cap = 0;
+      PP_CK(cudaMalloc(&ctx->d_gterm, sizeof(double) * 9 * n_st));
+      ctx->gterm_cap = n_st;
+    }
+    ds_host.assign(n_st * 3 * (size_t)n_mu, 0.0);
+  }
   PP_TRY(copy(ctx, n, lam, lam_Nt));
   ctx->last_gmres_adjoint = 0;
   for (int step = Nt - 1; step >= 0; --step) {
@@ -662,8 +698,9 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
       if (sv.JT) PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.JT, 0.0, dt, kap, y[i], 0, ctx->stream));
       else PP_CK(launch_stage_matvec<double>(m, ctx->tb, sv.J, 0.0, dt, kap, y[i], 1, ctx->stream));
       if (withF && dFdmu) {
-        // kappa_i . dr/ds and w . dQ/ds for the motion seeds s = theta, theta', h'
-        double sr[3], sq[3];
+        // kappa_i . dr/ds and dQ/ds for the motion seeds s = theta, theta', h'
+        const size_t st = (size_t)step * 3 + i;
+        double* gt = ctx->d_gterm + 9 * st;
         for (int s = 0; s < 3; ++s) {
           FrameT<Dual> fd;
           double cth = std::cos(mo.th), sth = std::sin(mo.th);
@@ -675,21 +712,16 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
           }
           fd.hd = Dual(fr.hd, s == 2 ? 1.0 : 0.0);
           PP_CK(launch_residual_dframe(m, ctx->tb, ctx->ph, fd, ui, dr, ctx->stream));
-          PP_CK(launch_dot<double>(n, kap, dr, ctx->d_scalar + 16 + s, ctx->d_partial, ctx->d_counter, ctx->stream));
+          PP_CK(launch_dot<double>(n, kap, dr, gt + s, ctx->d_partial, ctx->d_counter, ctx->stream));
           PP_CK(launch_qoi_dframe(m, ctx->tb, ctx->ph, fd, ui, ctx->d_elem, ctx->stream));
-          PP_CK(launch_colsum(mesh->ne, 2, ctx->d_elem, ctx->d_scalar + 20 + 2 * s, ctx->d_partial, ctx->d_counter,
+          PP_CK(launch_colsum(mesh->ne, 2, ctx->d_elem, gt + 3 + 2 * s, ctx->d_partial, ctx->d_counter,
                               ctx->stream));
-        }
-        PP_CK(cudaMemcpyAsync(ctx->h_scalar + 16, ctx->d_scalar + 16, 12 * sizeof(double), cudaMemcpyDeviceToHost,
-                              ctx->stream));
-        PP_CK(cudaStreamSynchronize(ctx->stream));
-        for (int s = 0; s < 3; ++s) {
-          sr[s] = ctx->h_scalar[16 + s];
-          sq[s] = w0 * ctx->h_scalar[20 + 2 * s] + w1 * ctx->h_scalar[21 + 2 * s];
         }
         for (int j = 0; j < n_mu; ++j) {
-          double ds[3] = {mo.dth[j], mo.dthd[j], mo.dhd[j]};
-          for (int s = 0; s < 3; ++s) grad[j] += dt * sr[s] * ds[s] + dt * ctx->b[i] * sq[s] * ds[s];
+          double* d = &ds_host[(st * n_mu + j) * 3];
+          d[0] = mo.dth[j];
+          d[1] = mo.dthd[j];
+          d[2] = mo.dhd[j];
         }
       }
     }
@@ -699,8 +731,31 @@ int adjoint_sweep(pp_ctx* ctx, const double* lam_Nt, const double* weights, doub
       PP_TRY(lincomb(ctx, n, lam, {1.0, dt * ctx->b[0], dt * ctx->b[1], dt * ctx->b[2]}, {lam, g[0], g[1], g[2]}));
   }
   PP_TRY(copy(ctx, n, lam0, lam));
+  std::vector<double> gterm;
+  if (withF && dFdmu) {
+    gterm.resize(9 * n_st);
+    PP_CK(cudaMemcpyAsync(gterm.data(), ctx->d_gterm, sizeof(double) * 9 * n_st, cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  }
   PP_CK(cudaStreamSynchronize(ctx->stream));
   PP_TRY(check_stream_kernels(ctx));
+  if (withF && dFdmu) {
+    // the same sums, in the same order, as the sweep's stage order (step Nt-1 .. 0, stage 2 .. 0)
+    for (int step = Nt - 1; step >= 0; --step)
+      for (int i = 2; i >= 0; --i) {
+        const size_t st = (size_t)step * 3 + i;
+        const double* gt = &gterm[9 * st];
+        double sr[3], sq[3];
+        for (int s = 0; s < 3; ++s) {
+          sr[s] = gt[s];
+          sq[s] = w0 * gt[3 + 2 * s] + w1 * gt[4 + 2 * s];
+        }
+        for (int j = 0; j < n_mu; ++j) {
+          const double* ds = &ds_host[(st * n_mu + j) * 3];
+          for (int s = 0; s < 3; ++s) grad[j] += dt * sr[s] * ds[s] + dt * ctx->b[i] * sq[s] * ds[s];
+        }
+      }
+  }
   if (dFdmu)
     for (int j = 0; j < n_mu; ++j) dFdmu[j] = withF ? grad[j] : 0.0;
   return PP_OK;

@@ -214,8 +214,8 @@ def lhs(n, lo, hi, seed):
 def experiment(config="c0", n_train=96, n_test=16, tol=1e-8, epochs=6000, seed=44):
     """Data generation with the GPU shooter, POD + network training, then per held-out mu
     the time to a periodic gradient (u0 with ||R|| <= tol, then the periodic adjoint for
-    J_E) by (a) plain FP64 from the steady-state cold start and (b) mixed precision from
-    the learned warm start."""
+    J_E) by (a) plain FP64 from the steady-state cold start, (b) mixed precision from the
+    learned warm start and (c) FP64 from the learned warm start."""
     from pp_inputs import CONFIGS, KIN_FOURIER6, MU_F6_BASE, MU_F6_SCALE, config_mesh
     c = CONFIGS[config]
     mesh = config_mesh(config)
@@ -256,9 +256,17 @@ def experiment(config="c0", n_train=96, n_test=16, tol=1e-8, epochs=6000, seed=4
         _, _, st_b, used, _ = shoot_with_warm_start(ctxs["mixed"], meshes["mixed"], mu, c["Nt"], tol, predictor=ws)
         _, g_b, _ = A.pp_periodic_adjoint(ctxs["mixed"], meshes["mixed"], mu, c["Nt"], w)
         t_b = time.perf_counter() - t0
+        # (c) FP64, learned warm start (the warm start's own effect)
+        t0 = time.perf_counter()
+        _, _, st_c, _, _ = shoot_with_warm_start(ctxs["fp64"], meshes["fp64"], mu, c["Nt"], tol, predictor=ws)
+        _, g_c, _ = A.pp_periodic_adjoint(ctxs["fp64"], meshes["fp64"], mu, c["Nt"], w)
+        t_c = time.perf_counter() - t0
         rows.append(dict(plain_newton=st_a["newton_iters"], plain_tangent_sweeps=st_a["krylov_iters"],
                          plain_s=t_a, learned_newton=st_b["newton_iters"],
                          learned_tangent_sweeps=st_b["krylov_iters"], learned_s=t_b,
+                         fp64_learned_newton=st_c["newton_iters"], fp64_learned_tangent_sweeps=st_c["krylov_iters"],
+                         fp64_learned_s=t_c,
+                         grad_rel_diff_fp64_learned=float(np.linalg.norm(g_c - g_a) / np.linalg.norm(g_a)),
                          first_residual_plain=st_a["residual"][0],
                          first_residual_learned=st_b.get("prediction_residual", st_b["residual"][0]),
                          grad_rel_diff=float(np.linalg.norm(g_b - g_a) / np.linalg.norm(g_a)), used=used))
