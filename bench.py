@@ -348,8 +348,8 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c, sustained):
     hbm = peaks["hbm_gbs"]
     if kernel.startswith("arnoldi"):
         # bytes of one fused Arnoldi step over k basis vectors of length n, counted at launch:
-        # (2k + 5) n words (two Gram-Schmidt passes and the scaling of the new basis vector;
-        # a selective second update is not counted); one cooperative launch per step
+        # (2k + 3) n words (projections, then the update written as the scaled new basis
+        # vector; a selective second pass is not counted); one cooperative launch per step
         ach = counted / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": None, "kernel": "k_arnoldi<KB,%s> (one fused Arnoldi step: Gram-Schmidt "

@@ -597,6 +597,19 @@ __device__ __forceinline__ void cta_reduce(S* v, int kb, double* bp, int j0) {
   }
 }
 
+// cta_reduce over KB (a multiple of 4, <= 40) values split into power-of-two pieces
+// (40 = 32 + 8, 28 = 16 + 8 + 4, ...): a reduce-scatter of P values costs about P FP64 adds
+// per lane, so the pieces cost about KB adds instead of the next power of two.
+template <int KB, int J0, class S>
+__device__ __forceinline__ void cta_reduce_pieces(S* v, int k, double* bp) {
+  if constexpr (KB > 0) {
+    constexpr int P = KB >= 32 ? 32 : (1 << ILog2<KB>::value);
+    const int valid = k - J0 < P ? k - J0 : P;
+    cta_reduce<P, S>(v + J0, valid > 0 ? valid : 0, bp, J0);
+    cta_reduce_pieces<KB - P, J0 + P, S>(v, k, bp);
+  }
+}
+
 // Grid level of the reduction of the CTA partials bp[0..nk).  Returns true in the one
 // CTA that holds the final sums in out[] (the last CTA to arrive).  The last CTA splits
 // the partial rows into CGS_T / nk' chunks per output, loads each chunk with all loads
@@ -793,11 +806,13 @@ __global__ void __launch_bounds__(CGS_T, 1) k_cgs(CgsArgs<S> a) {
 // (warp w sums outputs w, w + 8, ...; lanes stride over the CTAs, then a xor butterfly),
 // so all CTAs hold bitwise the same coefficients and no CTA waits for a last-arriving one.
 // Passes (k <= KB basis vectors in registers):
-//   1. h1 = V^T w and |w|^2
-//   2. w -= V h1, then h2 = V^T w if more than half of |w|^2 cancelled, else |w|^2
-//   3. (only if needed) w -= V h2, |w|^2
-// then v_k = w / |w| in every CTA, and CTA 0 applies the Givens update and writes the
-// convergence record to the pinned host ring.  Barrier waits are bounded (about a second);
+//   1. h1 = V^T w and |w|^2 (one exchange)
+//   2. if at most half of |w|^2 cancelled (|h1|^2 <= |w|^2 / 2, the selective
+//      reorthogonalization test): v_k = (w - V h1) / sqrt(|w|^2 - |h1|^2), no further
+//      exchange; else w -= V h1, h2 = V^T w (exchange), w -= V h2, |w|^2 (exchange),
+//      v_k = w / |w|
+// and CTA 0 applies the Givens update and writes the convergence record to the pinned
+// host ring.  Barrier waits are bounded (about a second);
 // an expired wait sets the error word, the convergence flag 8 and ends the kernel.
 constexpr unsigned long long kArnBarrierNs = 1000000000ull;
 constexpr int ARN_LD = CGS_MAXKB + 2;       // partial rows (outputs) per exchange
@@ -891,29 +906,31 @@ __device__ __forceinline__ bool arn_exchange(int nk, const double* bp, double* r
   constexpr int R = (ARN_NB + 31) / 32;
   constexpr int Q = (ARN_LD + NW - 1) / NW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nb = gridDim.x;
+  // outputs of this warp: j = warp + NW q for q < nq (warp-uniform, so only the warps and
+  // rounds that own an output spend FP64 adds; GB300 issues about 1.7 FP64 adds per clock
+  // per SM, so the reduction of the partials is not free)
+  const int nq = nk > warp ? (nk - warp + NW - 1) / NW : 0;
   double s[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const int j = warp + NW * q;
     double acc = 0.0;
-    if (j < nk) {
+    if (q < nq) {
+      const double* col = region + (size_t)(warp + NW * q) * ARN_NB;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int b = lane + 32 * r;
-        if (b < nb) acc += __ldcg(region + (size_t)j * ARN_NB + b);
+        if (b < nb) acc += __ldcg(col + b);
       }
     }
     s[q] = acc;
   }
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
+    if (q < nq) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-      if (warp + NW * q < nk) out[warp + NW * q] = s[q];
+      for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+      if (lane == 0) out[warp + NW * q] = s[q];
+    }
   }
   __syncthreads();
   return true;
@@ -921,7 +938,6 @@ __device__ __forceinline__ bool arn_exchange(int nk, const double* bp, double* r
 
 template <int KB, class S>
 __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
-  constexpr int K2 = Pow2Up<KB>::value;
   __shared__ double bp[CGS_MAXK + 1];
   __shared__ double red[CGS_MAXKB + 1];  // result of the last exchange
   __shared__ double hA[KB], hB[KB];      // h1, h2 (zero beyond k)
@@ -945,9 +961,9 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
   bool ok;
   // pass 1: h1 = V^T w, |w|^2
   {
-    S acc[K2], accs[1] = {S(0)};
+    S acc[KB], accs[1] = {S(0)};
 #pragma unroll
-    for (int t = 0; t < K2; ++t) acc[t] = S(0);
+    for (int t = 0; t < KB; ++t) acc[t] = S(0);
     for (int64_t i = i0; i < n; i += stride) {
       S v[KB];
 #pragma unroll
@@ -957,15 +973,21 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
       for (int t = 0; t < KB; ++t) acc[t] += v[t] * s;
       accs[0] += s * s;
     }
-    cta_reduce<K2, S>(acc, k, bp, 0);
+    cta_reduce_pieces<KB, 0, S>(acc, k, bp);
     cta_reduce<1, S>(accs, 1, bp, k);
   }
   ok = arn_exchange(k + 1, bp, region0, a.bar, e0 + 1, red);
+  double nrm2 = 0.0;
+  S* __restrict__ vn = a.vnext;
   if (ok) {
+    __shared__ double s_hh;
     if (threadIdx.x < 32) {
       double hh;
       const bool nd = reorth_needed_warp0(red, red[k], k, hh);
-      if (threadIdx.x == 0) s_need = nd ? 1 : 0;
+      if (threadIdx.x == 0) {
+        s_need = nd ? 1 : 0;
+        s_hh = hh;
+      }
     }
     for (int t = threadIdx.x; t < KB; t += CGS_T) {
       hA[t] = t < k ? red[t] : 0.0;
@@ -973,11 +995,13 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
     }
     __syncthreads();
     const bool need = s_need != 0;
-    // pass 2: w -= V h1, then V^T w (second pass) or |w|^2
-    {
-      S acc[K2];
-#pragma unroll
-      for (int t = 0; t < K2; ++t) acc[t] = S(0);
+    if (!need) {
+      // at most half of |w|^2 cancelled: one update, and |w - V h1|^2 = |w|^2 - |h1|^2 (the
+      // basis is orthonormal to working precision; the subtraction keeps at least half),
+      // so v_k = (w - V h1) / |w - V h1| needs no second reduction
+      nrm2 = red[k] - s_hh;
+      const double hn = sqrt(fmax(nrm2, 0.0));
+      const S inv = S(hn > 0.0 ? 1.0 / hn : 0.0);
       for (int64_t i = i0; i < n; i += stride) {
         S v[KB];
 #pragma unroll
@@ -985,35 +1009,52 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
         S s = w[i];
 #pragma unroll
         for (int t = 0; t < KB; ++t) s -= S(hA[t]) * v[t];
-        w[i] = s;
-        if (need) {
+        vn[i] = inv * s;
+      }
+    } else {
+      // pass 2: w -= V h1, h2 = V^T w
+      {
+        S acc[KB];
+#pragma unroll
+        for (int t = 0; t < KB; ++t) acc[t] = S(0);
+        for (int64_t i = i0; i < n; i += stride) {
+          S v[KB];
+#pragma unroll
+          for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
+          S s = w[i];
+#pragma unroll
+          for (int t = 0; t < KB; ++t) s -= S(hA[t]) * v[t];
+          w[i] = s;
 #pragma unroll
           for (int t = 0; t < KB; ++t) acc[t] += v[t] * s;
-        } else {
+        }
+        cta_reduce_pieces<KB, 0, S>(acc, k, bp);
+      }
+      ok = arn_exchange(k, bp, region1, a.bar, e0 + 2, red);
+      if (ok) {
+        for (int t = threadIdx.x; t < k; t += CGS_T) hB[t] = red[t];
+        __syncthreads();
+        // pass 3: w -= V h2, |w|^2
+        S acc[1] = {S(0)};
+        for (int64_t i = i0; i < n; i += stride) {
+          S v[KB];
+#pragma unroll
+          for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
+          S s = w[i];
+#pragma unroll
+          for (int t = 0; t < KB; ++t) s -= S(hB[t]) * v[t];
+          w[i] = s;
           acc[0] += s * s;
         }
+        cta_reduce<1, S>(acc, 1, bp, 0);
+        ok = arn_exchange(1, bp, region0, a.bar, e0 + 3, red);
       }
-      if (need) cta_reduce<K2, S>(acc, k, bp, 0);
-      else cta_reduce<1, S>(acc, 1, bp, 0);
-    }
-    ok = arn_exchange(need ? k : 1, bp, region1, a.bar, e0 + 2, red);
-    if (ok && need) {
-      for (int t = threadIdx.x; t < k; t += CGS_T) hB[t] = red[t];
-      __syncthreads();
-      // pass 3: w -= V h2, |w|^2
-      S acc[1] = {S(0)};
-      for (int64_t i = i0; i < n; i += stride) {
-        S v[KB];
-#pragma unroll
-        for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
-        S s = w[i];
-#pragma unroll
-        for (int t = 0; t < KB; ++t) s -= S(hB[t]) * v[t];
-        w[i] = s;
-        acc[0] += s * s;
+      if (ok) {
+        nrm2 = red[0];
+        const double hn = sqrt(fmax(nrm2, 0.0));
+        const S inv = S(hn > 0.0 ? 1.0 / hn : 0.0);
+        for (int64_t i = i0; i < n; i += stride) vn[i] = inv * w[i];
       }
-      cta_reduce<1, S>(acc, 1, bp, 0);
-      ok = arn_exchange(1, bp, region0, a.bar, e0 + 3, red);
     }
   }
   if (!ok) {
@@ -1024,14 +1065,6 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
       }
     }
     return;
-  }
-  const double nrm2 = red[0];
-  // v_k = w / |w| (the scaling of k_scale_dev with stat[3] = 1 / hn)
-  {
-    const double hn = sqrt(fmax(nrm2, 0.0));
-    const S inv = S(hn > 0.0 ? 1.0 / hn : 0.0);
-    S* __restrict__ vn = a.vnext;
-    for (int64_t i = i0; i < n; i += stride) vn[i] = inv * w[i];
   }
   if (blockIdx.x != 0) return;
   for (int t = threadIdx.x; t < k; t += CGS_T) {
@@ -1355,9 +1388,10 @@ cudaError_t launch_arnoldi_step(int64_t n, const S* V, int64_t ldv, int k, S* w,
                                 double* H, double* cs, double* sn, double* g, double* stat, cudaStream_t st) {
   if (k < 1 || k > CGS_MAXKB) return cudaErrorInvalidValue;
   const int kind = sizeof(S) == 8 ? PP_K_ARNOLDI : PP_K_ARNOLDI32;
-  // algorithmic traffic: V and w read for the projections; V and w read and w written for
-  // the update and norm; w read and v_k written for the scaling
-  prof_add_bytes(kind, (2.0 * k + 5.0) * (double)n * sizeof(S), 1);
+  // algorithmic traffic of the common path: V and w read for the projections, V and w
+  // read and v_k written for the update and scaling (a second pass, when the
+  // reorthogonalization test asks for it, is not counted)
+  prof_add_bytes(kind, (2.0 * k + 3.0) * (double)n * sizeof(S), 1);
   ProfScope ps(kind, st);
   ArnArgs<S> a{};
   a.n = n;
