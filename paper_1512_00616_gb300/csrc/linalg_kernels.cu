@@ -500,9 +500,10 @@ struct GivensArgs {
   double* sn;
   double* g;
   double* stat;  // {res, tol, hn, 1/hn, beta, 1/beta, flag, j}
+  double shift = 0.0;  // added to H(j, j): Arnoldi ran on A - shift I
 };
 
-// Hessenberg column j = h1 + h2 and norm hn, previous rotations, new rotation, residual
+// Hessenberg column j = h1 + h2 (+ shift on the diagonal) and norm hn, previous rotations, new rotation, residual
 // estimate |g[j+1]| and stop flag (1 converged, 2 breakdown, 4 non-finite).  Loads are
 // staged in shared memory by the whole block; the rotation chain runs on one thread.
 __device__ __forceinline__ void givens_update(const GivensArgs& a, double nrm2) {
@@ -510,6 +511,7 @@ __device__ __forceinline__ void givens_update(const GivensArgs& a, double nrm2) 
   const int j = a.j, m = a.m;
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
     col[i] = a.h1[i] + a.h2[i];
+    if (i == j) col[i] += a.shift;
     if (i < j) {
       c_s[i] = a.cs[i];
       s_s[i] = a.sn[i];
@@ -1358,8 +1360,8 @@ cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k
 template <class S>
 cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w, double* h1, double* h2,
                                  double* nrm, double* partial, unsigned* counter, int j, int m, double* H, double* cs,
-                                 double* sn, double* g, double* stat, cudaStream_t st) {
-  const GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat};
+                                 double* sn, double* g, double* stat, double shift, cudaStream_t st) {
+  const GivensArgs gv{j, m, h1, h2, H, cs, sn, g, stat, shift};
   const int kind = sizeof(S) == 8 ? PP_K_ARNOLDI : PP_K_ARNOLDI32;
   // algorithmic traffic of one classical Gram-Schmidt pass: V and w read for the projections,
   // V and w read and w written for the update and norm
@@ -1385,7 +1387,8 @@ cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w
 template <class S>
 cudaError_t launch_arnoldi_step(int64_t n, const S* V, int64_t ldv, int k, S* w, S* vnext, double* h1, double* h2,
                                 double* nrm, double* arn_partial, unsigned* arn_bar, double* host_stat, int j, int m,
-                                double* H, double* cs, double* sn, double* g, double* stat, cudaStream_t st) {
+                                double* H, double* cs, double* sn, double* g, double* stat, double shift,
+                                cudaStream_t st) {
   if (k < 1 || k > CGS_MAXKB) return cudaErrorInvalidValue;
   const int kind = sizeof(S) == 8 ? PP_K_ARNOLDI : PP_K_ARNOLDI32;
   // algorithmic traffic of the common path: V and w read for the projections, V and w
@@ -1406,7 +1409,7 @@ cudaError_t launch_arnoldi_step(int64_t n, const S* V, int64_t ldv, int k, S* w,
   a.partial = arn_partial;
   a.bar = arn_bar;
   a.host_stat = host_stat;
-  a.gv = GivensArgs{j, m, h1, h2, H, cs, sn, g, stat};
+  a.gv = GivensArgs{j, m, h1, h2, H, cs, sn, g, stat, shift};
   // grid <= SM count and one CTA per SM: every CTA is resident, which the cooperative launch
   // checks (it fails rather than start a grid that could wait on a CTA that never runs)
   const int grid = cgs_blocks(n);
@@ -1476,10 +1479,10 @@ cudaError_t launch_scale(int64_t n, double* y, double a, const double* x, cudaSt
                                              cudaStream_t);                                                     \
   template cudaError_t launch_arnoldi_step<S>(int64_t, const S*, int64_t, int, S*, S*, double*, double*, double*,    \
                                              double*, unsigned*, double*, int, int, double*, double*, double*,      \
-                                             double*, double*, cudaStream_t);                                       \
+                                             double*, double*, double, cudaStream_t);                               \
   template cudaError_t launch_arnoldi_ortho<S>(int64_t, const S*, int64_t, int, S*, double*, double*, double*,  \
                                                  double*, unsigned*, int, int, double*, double*, double*, double*,  \
-                                                 double*, cudaStream_t);                                            \
+                                                 double*, double, cudaStream_t);                                    \
   template cudaError_t launch_update_norm2_givens<S>(int64_t, const S*, int64_t, int, const double*, S*, double*,   \
                                                      double*, unsigned*, int, int, const double*, const double*,    \
                                                      double*, double*, double*, double*, double*, cudaStream_t);    \

@@ -187,12 +187,14 @@ cudaError_t launch_update_norm2(int64_t n, const S* V, int64_t ldv, int k, const
 // One fused Arnoldi step (cooperative launch, k <= 40): classical Gram-Schmidt with
 // selective reorthogonalization, the Givens update, v_k = w / |w| and the convergence
 // record (stat[0..8)) also written to host_stat (a device-visible pinned slot, or null).
+// shift: the Krylov operator is A - shift I; H(j, j) gets shift back.
 // arn_partial holds arnoldi_partial_words() doubles; arn_bar arnoldi_barrier_words() zeroed
 // words (arrival count, release epoch, and an error word set when a barrier wait expired).
 template <class S>
 cudaError_t launch_arnoldi_step(int64_t n, const S* V, int64_t ldv, int k, S* w, S* vnext, double* h1, double* h2,
                                 double* nrm, double* arn_partial, unsigned* arn_bar, double* host_stat, int j, int m,
-                                double* H, double* cs, double* sn, double* g, double* stat, cudaStream_t st);
+                                double* H, double* cs, double* sn, double* g, double* stat, double shift,
+                                cudaStream_t st);
 size_t arnoldi_partial_words();
 int arnoldi_barrier_words();       // size of arn_bar in 32-bit words
 int arnoldi_barrier_error_word();  // index of the error word in arn_bar
@@ -200,7 +202,7 @@ constexpr int kArnoldiFusedMaxK = 40;
 template <class S>
 cudaError_t launch_arnoldi_ortho(int64_t n, const S* V, int64_t ldv, int k, S* w, double* h1, double* h2,
                                  double* nrm, double* partial, unsigned* counter, int j, int m, double* H, double* cs,
-                                 double* sn, double* g, double* stat, cudaStream_t st);
+                                 double* sn, double* g, double* stat, double shift, cudaStream_t st);
 template <class S>
 cudaError_t launch_update_norm2_givens(int64_t n, const S* V, int64_t ldv, int k, const double* h, S* w, double* out,
                                        double* partial, unsigned* counter, int j, int m, const double* h1,
@@ -215,7 +217,8 @@ cudaError_t launch_colsum(int ne, int k, const double* per_elem, double* out, do
                           cudaStream_t st);
 
 // TMA-staged block-row products (stream_kernels.cu): nblk = 4, the stage operator
-// y = alpha M x + beta J x; nblk = 1, the block product y = A x.  Normal products only.
+// y = alpha M x + beta J x; nblk = 3, the folded operator y = x + B x (beta != 0) or its
+// shifted form y = B x (beta = 0); nblk = 1, the block product y = A x.  Normal products only.
 template <class S>
 bool stream_rows_supported(int nb, const S* B, const S* x, const S* y);
 template <class S>

@@ -107,7 +107,8 @@ int copy(pp_ctx* ctx, int64_t n, S* y, const S* x) {
 // enqueued past convergence is simply not used (its column is beyond ncols).
 template <class S>
 int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const S* b, S* x, double rtol,
-          double atol, int maxit, int* iters, double* res_out, bool flexible = false, bool warm = false) {
+          double atol, int maxit, int* iters, double* res_out, bool flexible = false, bool warm = false,
+          double shift = 0.0) {
   const int64_t n = K.n;
   const int m = K.m;
   double* d_h1 = K.d_h;
@@ -121,7 +122,8 @@ int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const
     PP_CK(launch_dot<S>(n, b, b, d_nrm, ctx->d_partial, ctx->d_counter, ctx->stream));
     PP_CK(launch_gmres_init(d_nrm, rtol, atol, 1, m, K.d_g, K.d_stat, ctx->stream));
     PP_TRY(A(x, K.w));
-    PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
+    if (shift != 0.0) PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0, -shift}, {b, K.w, x}));
+    else PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
     first = false;
   } else {
     PP_CK(cudaMemsetAsync(x, 0, sizeof(S) * n, ctx->stream));
@@ -152,11 +154,11 @@ int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const
         // one cooperative launch: orthogonalization, Givens, scaling, record into the ring
         PP_CK(launch_arnoldi_step<S>(n, K.V, n, j + 1, K.w, vnext, d_h1, d_h2, d_nrm, ctx->d_arn, ctx->d_arn_bar,
                                      K.h_h_dev + 8 * (j % kRing), j, m, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat,
-                                     ctx->stream));
+                                     shift, ctx->stream));
         PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
       } else {
         PP_CK(launch_arnoldi_ortho<S>(n, K.V, n, j + 1, K.w, d_h1, d_h2, d_nrm, ctx->d_partial, ctx->d_counter, j,
-                                      m, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, ctx->stream));
+                                      m, K.d_H, K.d_cs, K.d_sn, K.d_g, K.d_stat, shift, ctx->stream));
         PP_CK(cudaMemcpyAsync(slot, K.d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         PP_CK(cudaEventRecord(K.ev[j % kRing], ctx->stream));
         PP_CK(launch_scale_dev<S>(n, vnext, K.d_stat + 3, K.w, ctx->stream));
@@ -200,7 +202,8 @@ int gmres(pp_ctx* ctx, KrylovT<S>& K, const OpT<S>& A, const OpT<S>& prec, const
     if (total >= maxit) break;
     // restart from the true residual r = b - A x
     PP_TRY(A(x, K.w));
-    PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
+    if (shift != 0.0) PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0, -shift}, {b, K.w, x}));
+    else PP_TRY(lincomb<S>(ctx, n, K.r, {1.0, -1.0}, {b, K.w}));
   }
   if (iters) *iters = total;
   if (res_out) *res_out = res;
@@ -231,12 +234,15 @@ int stage_solve32(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int tra
   if (Bf) {
     // folded operator: GMRES on (I + B) y = b, then x = D^{-1} y (D^{-T} y)
     float* yv = ctx->k32.t;
+    // Krylov recurrence on B (Arnoldi adds the unit shift back to H): w = B v keeps most of
+    // its norm after the projections, where w = (I + B) v cancels down to |B v|
     OpT<float> A = [&](const float* in, float* out) {
       ProfScope ps(PP_K_STAGE_OP32, ctx->stream);
-      PP_CK(launch_stream_rows<float>(m, ctx->tb, ctx->tb.nb, 3, Bf, 0.0, 1.0, in, out, ctx->stream));
+      PP_CK(launch_stream_rows<float>(m, ctx->tb, ctx->tb.nb, 3, Bf, 0.0, 0.0, in, out, ctx->stream));
       return PP_OK;
     };
-    int st = gmres<float>(ctx, ctx->k32, A, OpT<float>(), b, yv, rtol, 0.0, maxit, iters, nullptr);
+    int st = gmres<float>(ctx, ctx->k32, A, OpT<float>(), b, yv, rtol, 0.0, maxit, iters, nullptr, false, false,
+                          1.0);
     if (st != PP_OK && st != PP_ENOCONV) return st;
     PP_CK(launch_block_apply<float>(m, ctx->tb.nb, trans ? sv.AT32 : sv.A32, yv, x, 0, ctx->stream));
     return PP_OK;  // an inexact inner / Newton solve is acceptable
@@ -297,15 +303,16 @@ int stage_solve(pp_ctx* ctx, const pp_mesh* mesh, const StageView& sv, int trans
   const double* Bf = trans ? sv.BT : sv.BN;
   if (Bf) {
     double* yv = ctx->kin.t;  // unused by GMRES without a preconditioner
+    // Krylov recurrence on B, shifted back in H (see stage_solve32)
     Op A = [&](const double* in, double* out) {
       ProfScope ps(PP_K_STAGE_OP, ctx->stream);
-      PP_CK(launch_stream_rows<double>(m, ctx->tb, ctx->tb.nb, 3, Bf, 0.0, 1.0, in, out, ctx->stream));
+      PP_CK(launch_stream_rows<double>(m, ctx->tb, ctx->tb.nb, 3, Bf, 0.0, 0.0, in, out, ctx->stream));
       return PP_OK;
     };
     // warm start (linear sweeps): the same stage's y of the previous step is the initial guess
     if (ywarm && use_warm) PP_TRY(copy(ctx, n, yv, ywarm));
     int st = gmres<double>(ctx, ctx->kin, A, Op(), b, yv, rtol, atol, ctx->cfg.gmres_maxit, iters, nullptr, false,
-                           ywarm && use_warm);
+                           ywarm && use_warm, 1.0);
     if (st != PP_OK && st != PP_ENOCONV) return st;
     if (ywarm) PP_TRY(copy(ctx, n, ywarm, yv));
     if (!trans) PP_CK(launch_block_apply<double>(m, ctx->tb.nb, sv.Ainv, yv, x, 0, ctx->stream));

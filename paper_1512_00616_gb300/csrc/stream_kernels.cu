@@ -236,7 +236,12 @@ __global__ void __launch_bounds__(StreamShape<NB, NBLK, S>::THREADS)
     consumer_sync(32 * CW);
     if (p < NB) {
       S s;
-      if (NBLK == 3) s = ring[(size_t)((li * 3) % R) * UNIT + NB * NB + NB + p] + (red[p] + red[NB + p] + red[2 * NB + p]);
+      if (NBLK == 3) {
+        // y = beta x + B x: beta = 1 gives the folded operator I + B, beta = 0 the
+        // shifted Krylov operator B
+        const S bx = red[p] + red[NB + p] + red[2 * NB + p];
+        s = beta != 0.0 ? ring[(size_t)((li * 3) % R) * UNIT + NB * NB + NB + p] + bx : bx;
+      }
       else s = (red[p] + red[NB + p]) + (red[2 * NB + p] + red[3 * NB + p]);
       if (NBLK == 4) {
         s *= S(beta);
