@@ -949,8 +949,14 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
   const S* __restrict__ V = a.V;
   S* __restrict__ w = a.w;
   const int64_t ldv = a.ldv;
-  const int64_t stride = (int64_t)gridDim.x * CGS_T;
-  const int64_t i0 = (int64_t)blockIdx.x * CGS_T + threadIdx.x;
+  // contiguous, balanced slices (a multiple of 32 entries per CTA): every CTA reaches the
+  // barriers with the same work, where a grid-stride loop leaves the first n mod (grid x
+  // CGS_T) / CGS_T CTAs with one more entry per thread than the rest
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const int64_t lo = (int64_t)blockIdx.x * chunk < n ? (int64_t)blockIdx.x * chunk : n;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  const int64_t stride = CGS_T;
+  const int64_t i0 = lo + threadIdx.x;
   double* region0 = a.partial;
   double* region1 = a.partial + (size_t)ARN_LD * ARN_NB;
   // epoch before this launch's first barrier (stable: it only moves inside a barrier,
@@ -966,7 +972,7 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
     S acc[KB], accs[1] = {S(0)};
 #pragma unroll
     for (int t = 0; t < KB; ++t) acc[t] = S(0);
-    for (int64_t i = i0; i < n; i += stride) {
+    for (int64_t i = i0; i < hi; i += stride) {
       S v[KB];
 #pragma unroll
       for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
@@ -1004,7 +1010,7 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
       nrm2 = red[k] - s_hh;
       const double hn = sqrt(fmax(nrm2, 0.0));
       const S inv = S(hn > 0.0 ? 1.0 / hn : 0.0);
-      for (int64_t i = i0; i < n; i += stride) {
+      for (int64_t i = i0; i < hi; i += stride) {
         S v[KB];
 #pragma unroll
         for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
@@ -1019,7 +1025,7 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
         S acc[KB];
 #pragma unroll
         for (int t = 0; t < KB; ++t) acc[t] = S(0);
-        for (int64_t i = i0; i < n; i += stride) {
+        for (int64_t i = i0; i < hi; i += stride) {
           S v[KB];
 #pragma unroll
           for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
@@ -1038,7 +1044,7 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
         __syncthreads();
         // pass 3: w -= V h2, |w|^2
         S acc[1] = {S(0)};
-        for (int64_t i = i0; i < n; i += stride) {
+        for (int64_t i = i0; i < hi; i += stride) {
           S v[KB];
 #pragma unroll
           for (int t = 0; t < KB; ++t) v[t] = (t < k) ? V[(int64_t)t * ldv + i] : S(0);
@@ -1055,7 +1061,7 @@ __global__ void __launch_bounds__(CGS_T, 1) k_arnoldi(ArnArgs<S> a) {
         nrm2 = red[0];
         const double hn = sqrt(fmax(nrm2, 0.0));
         const S inv = S(hn > 0.0 ? 1.0 / hn : 0.0);
-        for (int64_t i = i0; i < n; i += stride) vn[i] = inv * w[i];
+        for (int64_t i = i0; i < hi; i += stride) vn[i] = inv * w[i];
       }
     }
   }
