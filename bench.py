@@ -368,7 +368,7 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c, sustained):
         return {"bound": "alu", "achieved": ach, "peak": fp64_tflops, "unit": "TFLOP/s",
                 "frac": ach / fp64_tflops if fp64_tflops else None,
                 "traffic": MEASURED_TRAFFIC.get((kernel, res["config"])),
-                "kernel": "k_stream_rows<%d,3,double> (I + B, folded block-Jacobi)" % nb,
+                "kernel": "k_stream_rows<%d,3,double> (B = (M - cJ) D^-1 - I, folded block-Jacobi)" % nb,
                 "launches": launches, "avg_us": t * 1e6, "hbm_gbs_equiv": byts / t / 1e9,
                 "peak_source": "pp_measure_fp64_peak_clock (16-chain FMA probe, measured in this run)"}
     ach = byts / t / 1e9
