@@ -53,6 +53,10 @@ extern "C" {
 #define PP_KIN_HEAVE_PITCH 0 /* mu = (h0, theta0, phi): h = h0 sin(wt), theta = theta0 sin(wt + phi) */
 #define PP_KIN_FOURIER6 1    /* mu = (a1, b1, a2, al1, be1, al2): h = a1 sin wt + b1 cos wt + a2 sin 2wt,
                                 theta = al1 sin wt + be1 cos wt + al2 sin 2wt;  w = 2 pi / T */
+#define PP_KIN_SPLINE8 2     /* Sec. 6.2, Eq. mirror: mu = (h0, h1, h2, h3, th0, th1, th2, th3), the knots at
+                                t = 0, T/8, T/4, 3T/8; h and theta are the periodic cubic splines through the
+                                8 equally spaced knots (f0, f1, f2, f3, -f0, -f1, -f2, -f3), so that
+                                f(t + T/2) = -f(t) */
 
 typedef struct pp_ctx pp_ctx;
 typedef struct pp_mesh pp_mesh;
@@ -148,6 +152,14 @@ int pp_ogrid_generate(int n_theta, int n_r, double r_far, uint64_t seed, double*
 int pp_mesh_ogrid(pp_ctx* ctx, int n_theta, int n_r, double r_far, uint64_t seed, pp_mesh** out);
 /* ne, np (nodes per element) and nu = ne*4*np; any output may be NULL. */
 int pp_mesh_info(const pp_mesh* mesh, int* ne, int* np, int64_t* nu);
+
+/* The prescribed motion that enters the rigid map (Eq. defmap): out[0..2] = (theta, theta',
+   h') at time t for the kinematics mode kin (PP_KIN_*, Sec. 6.1 single Fourier mode or the
+   Sec. 6.2 mirrored splines), then out[3 + 3 j .. 5 + 3 j] = d(theta, theta', h') / d mu_j
+   for j < n_mu -- the quantities every sweep and gradient takes from the same code.  Host
+   code (no GPU, no context).  mu: HOST [n_mu], n_mu the mode's parameter count (3, 6, 8);
+   out: HOST [3 + 3 n_mu].  Errors: PP_EINVAL (unknown mode, wrong n_mu, T <= 0, NULL). */
+int pp_motion_eval(int kin, double T, const double* mu, int n_mu, double t, double* out);
 
 /* Semi-discrete residual r(u, mu, t) of M du/dt = r (Eq. semidisc; ALE DG of
    Sec. 6).  u, r: DEVICE [N_u].  mu: HOST [n_mu]. */

@@ -50,6 +50,7 @@ from . import refelem
 
 KIN_HEAVE_PITCH = 0
 KIN_FOURIER6 = 1
+KIN_SPLINE8 = 2   # Sec. 6.2, Eq. mirror: knots of h and theta, 4 each
 CS_STEP = 1e-30
 C11_ETA = 10.0   # boundary penalty C11 = C11_ETA mu_visc / h with h = 2 |K| / |f|
 
@@ -150,6 +151,37 @@ def roe_flux(UL, UR, n, vn, gam):
 
 def dot_n(F, n):
     return F[..., 0] * n[..., None, 0] + F[..., 1] * n[..., None, 1]
+
+
+def periodic_cubic_spline(y, T, t):
+    """Value and first derivative at time t of the periodic cubic spline (period T) through
+    the m equally spaced knots (k T / m, y[k]).  Textbook construction: with d = T / m the
+    knot second derivatives M solve the cyclic system
+        M[k-1] + 4 M[k] + M[k+1] = 6 (y[k+1] - 2 y[k] + y[k-1]) / d^2,
+    and on [k d, (k+1) d] with s = (t - k d) / d
+        S = (1-s) y[k] + s y[k+1] + d^2/6 (((1-s)^3 - (1-s)) M[k] + (s^3 - s) M[k+1]).
+    y may be complex (complex-step derivatives with respect to the knot values)."""
+    y = np.asarray(y)
+    m = len(y)
+    d = T / m
+    A = 4.0 * np.eye(m) + np.roll(np.eye(m), 1, axis=1) + np.roll(np.eye(m), -1, axis=1)
+    rhs = 6.0 * (np.roll(y, -1) - 2.0 * y + np.roll(y, 1)) / d ** 2
+    M = np.linalg.solve(A, rhs)
+    tau = float(np.real(t)) % T
+    k = min(int(np.floor(tau / d)), m - 1)
+    s = (tau - k * d) / d
+    k1 = (k + 1) % m
+    val = (1 - s) * y[k] + s * y[k1] + d ** 2 / 6.0 * (((1 - s) ** 3 - (1 - s)) * M[k] + (s ** 3 - s) * M[k1])
+    der = (y[k1] - y[k]) / d + d / 6.0 * (-(3 * (1 - s) ** 2 - 1) * M[k] + (3 * s ** 2 - 1) * M[k1])
+    return val, der
+
+
+def mirrored_knots(half):
+    """Knot values over the whole period from the four free knots of the first half: the
+    mirror condition of Eq. mirror, f(t + T/2) = -f(t), fixes the second half (and the knot at
+    T/2, -f(0)), so the 8 equally spaced knots carry (f0, f1, f2, f3, -f0, -f1, -f2, -f3)."""
+    half = np.asarray(half)
+    return np.concatenate([half, -half])
 
 
 class DG:
@@ -278,6 +310,10 @@ class DG:
             hdot = h0 * w * np.cos(w * t)
             th = th0 * np.sin(w * t + ph)
             thdot = th0 * w * np.cos(w * t + ph)
+        elif self.kin == KIN_SPLINE8:
+            # mu = (h knots at t = 0, T/8, T/4, 3T/8; theta knots at the same times)
+            _, hdot = periodic_cubic_spline(mirrored_knots(mu[0:4]), self.T, t)
+            th, thdot = periodic_cubic_spline(mirrored_knots(mu[4:8]), self.T, t)
         else:
             a1, b1, a2, al1, be1, al2 = mu[0], mu[1], mu[2], mu[3], mu[4], mu[5]
             hdot = a1 * w * np.cos(w * t) - b1 * w * np.sin(w * t) + a2 * 2 * w * np.cos(2 * w * t)

@@ -27,7 +27,8 @@ side), mass matrix of the reference element.
 import numpy as np
 
 from . import blend
-from .dg import CS_STEP, DG, KIN_HEAVE_PITCH, inviscid_flux, normal_flux, roe_flux, viscous_flux
+from .dg import (CS_STEP, DG, KIN_HEAVE_PITCH, KIN_SPLINE8, inviscid_flux, mirrored_knots, normal_flux,
+                 periodic_cubic_spline, roe_flux, viscous_flux)
 
 
 class BlendedDG(DG):
@@ -43,6 +44,8 @@ class BlendedDG(DG):
         w = self.omega
         if self.kin == KIN_HEAVE_PITCH:
             return mu[0] * np.sin(w * t)
+        if self.kin == KIN_SPLINE8:
+            return periodic_cubic_spline(mirrored_knots(mu[0:4]), self.T, t)[0]
         return mu[0] * np.sin(w * t) + mu[1] * np.cos(w * t) + mu[2] * np.sin(2 * w * t)
 
     def nodal_map(self, mu, t):

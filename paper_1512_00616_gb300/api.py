@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpp.so")
 
 PP_OK, PP_EINVAL, PP_ENOMEM, PP_ENOCONV, PP_ENAN, PP_EBREAKDOWN, PP_ECUDA, PP_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-PP_KIN_HEAVE_PITCH, PP_KIN_FOURIER6 = 0, 1
+PP_KIN_HEAVE_PITCH, PP_KIN_FOURIER6, PP_KIN_SPLINE8 = 0, 1, 2
 PP_PREC_FP64, PP_PREC_MIXED = 0, 1
 STATUS_NAMES = {0: "PP_OK", -1: "PP_EINVAL", -2: "PP_ENOMEM", -3: "PP_ENOCONV", -4: "PP_ENAN",
                 -5: "PP_EBREAKDOWN", -6: "PP_ECUDA", -7: "PP_ESTATE"}
@@ -29,7 +29,7 @@ EXPORTED = [
     "pp_prof_select", "pp_prof_read", "pp_prof_counts", "pp_measure_fp64_peak", "pp_sweep_counts",
     "pp_shoot_fixed_point", "pp_periodic_adjoint_fixed_point", "pp_floquet", "pp_hessenberg_eigvals",
     "pp_ogrid_generate", "pp_mesh_ogrid", "pp_shoot_nk_batched", "pp_periodic_adjoint_batched",
-    "pp_periodic_adjoint_multi",
+    "pp_periodic_adjoint_multi", "pp_motion_eval",
     "pp_stage_apply", "pp_prof_also", "pp_prof_sample", "pp_prof_read_class", "pp_measure_fp64_peak_clock",
     # include/pp_learn.h
     "pp_gemm_f32", "pp_gemm_f64", "pp_bias_act_f32", "pp_gelu_backward_f32", "pp_colsum_f32", "pp_mse_f32",
@@ -83,6 +83,7 @@ def _load():
         "pp_mesh_create": (I, [P, dp, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), I, C.POINTER(P)]),
         "pp_mesh_destroy": (I, [P]),
         "pp_mesh_info": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_int64)]),
+        "pp_motion_eval": (I, [I, D, dp, I, D, dp]),
         "pp_residual": (I, [P, P, dp, I, D, P, P]),
         "pp_jacobian_blocks": (I, [P, P, dp, I, D, P, P]),
         "pp_qoi_rate": (I, [P, P, dp, I, D, P, dp]),
@@ -221,6 +222,16 @@ def pp_mesh_ogrid(ctx, n_theta, n_r, r_far=10.0, seed=0):
 
 def pp_mesh_destroy(mesh):
     _check(None, _lib.pp_mesh_destroy(mesh))
+
+
+def pp_motion_eval(kin, T, mu, t):
+    """(theta, theta', h') at time t and their derivatives d/dmu_j as a [1 + n_mu, 3] array."""
+    m, mp = _host(mu)
+    out = np.zeros(3 + 3 * len(m))
+    code = _lib.pp_motion_eval(int(kin), float(T), mp, len(m), float(t), out.ctypes.data_as(C.POINTER(C.c_double)))
+    if code != PP_OK:
+        raise PPError(code, "pp_motion_eval")
+    return out.reshape(1 + len(m), 3)
 
 
 def pp_mesh_info(mesh):

@@ -132,6 +132,8 @@ namespace pp {
 // host.cpp
 int set_error(pp_ctx* ctx, int code, const std::string& msg);
 Motion motion(const pp_ctx* ctx, const double* mu, int n_mu, double t);
+Motion motion_eval(int kin, double T, const double* mu, double t);  // no context needed
+int kin_param_count(int kin);                                      // -1 for an unknown mode
 FrameT<double> frame_of(const Motion& mo);
 int check_mu(pp_ctx* ctx, int n_mu);
 int ensure_workspace(pp_ctx* ctx, const pp_mesh* mesh);

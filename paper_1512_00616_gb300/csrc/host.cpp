@@ -202,11 +202,94 @@ static void dirk3(double A[3][3], double b[3], double c[3]) {
 }
 
 // ------------------------------------------------------------------ motion (Eq. defmap with Sec. 6.1 kinematics)
-Motion motion(const pp_ctx* ctx, const double* mu, int n_mu, double t) {
+namespace {
+
+// Mirrored spline kinematics (Sec. 6.2, Eq. mirror): h and theta are periodic cubic splines
+// through 8 equally spaced knots of the period whose second half repeats the first with the
+// opposite sign, f(t + T/2) = -f(t); the free values are the 4 knots of the first half.  The
+// spline is linear in the knot values, so it is a sum of 4 "mirrored cardinal" functions
+// (knot data e_j - e_{j+4}).  Knot second derivatives: the cyclic system
+// M[k-1] + 4 M[k] + M[k+1] = 6 (y[k+1] - 2 y[k] + y[k-1]) / d^2, d = T / 8, solved once for the
+// unit right-hand sides (Gauss-Jordan on the 8 x 8 matrix; its inverse scaled by 6 / d^2 later).
+constexpr int kKnots = 8;
+
+struct CyclicInverse {
+  double a[kKnots][kKnots];
+};
+
+const CyclicInverse& cyclic_inverse() {
+  static const CyclicInverse inv = [] {
+    CyclicInverse r{};
+    double m[kKnots][2 * kKnots] = {};
+    for (int k = 0; k < kKnots; ++k) {
+      m[k][k] = 4.0;
+      m[k][(k + 1) % kKnots] = 1.0;
+      m[k][(k + kKnots - 1) % kKnots] = 1.0;
+      m[k][kKnots + k] = 1.0;
+    }
+    // diagonally dominant: no pivoting needed
+    for (int c = 0; c < kKnots; ++c) {
+      const double piv = m[c][c];
+      for (int q = 0; q < 2 * kKnots; ++q) m[c][q] /= piv;
+      for (int r2 = 0; r2 < kKnots; ++r2) {
+        if (r2 == c) continue;
+        const double f = m[r2][c];
+        for (int q = 0; q < 2 * kKnots; ++q) m[r2][q] -= f * m[c][q];
+      }
+    }
+    for (int k = 0; k < kKnots; ++k)
+      for (int q = 0; q < kKnots; ++q) r.a[k][q] = m[k][kKnots + q];
+    return r;
+  }();
+  return inv;
+}
+
+// value and time derivative at t of the mirrored cardinal function of free knot j (0..3)
+void mirrored_cardinal(int j, double T, double t, double* val, double* der) {
+  const double d = T / kKnots;
+  double y[kKnots] = {};
+  y[j] = 1.0;
+  y[j + kKnots / 2] = -1.0;
+  double rhs[kKnots];
+  for (int k = 0; k < kKnots; ++k)
+    rhs[k] = 6.0 * (y[(k + 1) % kKnots] - 2.0 * y[k] + y[(k + kKnots - 1) % kKnots]) / (d * d);
+  const CyclicInverse& inv = cyclic_inverse();
+  double M[kKnots];
+  for (int k = 0; k < kKnots; ++k) {
+    double acc = 0.0;
+    for (int q = 0; q < kKnots; ++q) acc += inv.a[k][q] * rhs[q];
+    M[k] = acc;
+  }
+  double tau = std::fmod(t, T);
+  if (tau < 0.0) tau += T;
+  int k = (int)std::floor(tau / d);
+  if (k > kKnots - 1) k = kKnots - 1;
+  if (k < 0) k = 0;
+  const double s = (tau - k * d) / d, r = 1.0 - s;
+  const int k1 = (k + 1) % kKnots;
+  *val = r * y[k] + s * y[k1] + d * d / 6.0 * ((r * r * r - r) * M[k] + (s * s * s - s) * M[k1]);
+  *der = (y[k1] - y[k]) / d + d / 6.0 * (-(3.0 * r * r - 1.0) * M[k] + (3.0 * s * s - 1.0) * M[k1]);
+}
+
+}  // namespace
+
+int kin_param_count(int kin) {
+  switch (kin) {
+    case PP_KIN_HEAVE_PITCH:
+      return 3;
+    case PP_KIN_FOURIER6:
+      return 6;
+    case PP_KIN_SPLINE8:
+      return 8;
+    default:
+      return -1;
+  }
+}
+
+Motion motion_eval(int kin, double T, const double* mu, double t) {
   Motion mo{};
-  (void)n_mu;
-  const double w = 2.0 * M_PI / ctx->cfg.T;
-  if (ctx->cfg.kin == PP_KIN_HEAVE_PITCH) {
+  const double w = 2.0 * M_PI / T;
+  if (kin == PP_KIN_HEAVE_PITCH) {
     double h0 = mu[0], th0 = mu[1], ph = mu[2];
     double cw = std::cos(w * t), sp = std::sin(w * t + ph), cp = std::cos(w * t + ph);
     mo.hd = h0 * w * cw;
@@ -217,6 +300,18 @@ Motion motion(const pp_ctx* ctx, const double* mu, int n_mu, double t) {
     mo.dth[2] = th0 * cp;
     mo.dthd[1] = w * cp;
     mo.dthd[2] = -th0 * w * sp;
+  } else if (kin == PP_KIN_SPLINE8) {
+    // mu = (h knots at t = 0, T/8, T/4, 3T/8; theta knots at the same times)
+    for (int j = 0; j < kKnots / 2; ++j) {
+      double a, da;
+      mirrored_cardinal(j, T, t, &a, &da);
+      mo.hd += mu[j] * da;
+      mo.th += mu[4 + j] * a;
+      mo.thd += mu[4 + j] * da;
+      mo.dhd[j] = da;
+      mo.dth[4 + j] = a;
+      mo.dthd[4 + j] = da;
+    }
   } else {
     double s1 = std::sin(w * t), c1 = std::cos(w * t), s2 = std::sin(2 * w * t), c2 = std::cos(2 * w * t);
     mo.hd = mu[0] * w * c1 - mu[1] * w * s1 + mu[2] * 2 * w * c2;
@@ -235,6 +330,11 @@ Motion motion(const pp_ctx* ctx, const double* mu, int n_mu, double t) {
   return mo;
 }
 
+Motion motion(const pp_ctx* ctx, const double* mu, int n_mu, double t) {
+  (void)n_mu;
+  return motion_eval(ctx->cfg.kin, ctx->cfg.T, mu, t);
+}
+
 FrameT<double> frame_of(const Motion& mo) {
   FrameT<double> f;
   double c = std::cos(mo.th), s = std::sin(mo.th);
@@ -251,7 +351,7 @@ FrameT<double> frame_of(const Motion& mo) {
 }
 
 int check_mu(pp_ctx* ctx, int n_mu) {
-  int need = ctx->cfg.kin == PP_KIN_HEAVE_PITCH ? 3 : 6;
+  const int need = kin_param_count(ctx->cfg.kin);
   if (n_mu != need) return set_error(ctx, PP_EINVAL, "n_mu does not match the kinematics mode");
   return PP_OK;
 }
@@ -437,6 +537,21 @@ extern "C" {
 
 const char* pp_version(void) { return "libpp 0.1 (sm_103a, FP64)"; }
 
+int pp_motion_eval(int kin, double T, const double* mu, int n_mu, double t, double* out) {
+  const int need = kin_param_count(kin);
+  if (need < 0 || n_mu != need || !(T > 0) || !mu || !out) return PP_EINVAL;
+  const Motion mo = motion_eval(kin, T, mu, t);
+  out[0] = mo.th;
+  out[1] = mo.thd;
+  out[2] = mo.hd;
+  for (int j = 0; j < n_mu; ++j) {
+    out[3 + 3 * j] = mo.dth[j];
+    out[4 + 3 * j] = mo.dthd[j];
+    out[5 + 3 * j] = mo.dhd[j];
+  }
+  return PP_OK;
+}
+
 void pp_config_default(pp_config* c) {
   if (!c) return;
   std::memset(c, 0, sizeof(*c));
@@ -472,7 +587,7 @@ int pp_create(const pp_config* cfg, pp_ctx** out) {
   if (!cfg || !out) return PP_EINVAL;
   if (cfg->p < 1 || cfg->p > kMaxP || cfg->gmres_restart < 1 || cfg->gmres_restart > 60 || cfg->nk_restart < 1 ||
       cfg->nk_restart > 60 || cfg->adj_restart < 1 || cfg->adj_restart > 60 || !(cfg->T > 0) || !(cfg->Re > 0) ||
-      !(cfg->Mach > 0) || (cfg->kin != PP_KIN_HEAVE_PITCH && cfg->kin != PP_KIN_FOURIER6) ||
+      !(cfg->Mach > 0) || kin_param_count(cfg->kin) < 0 ||
       (cfg->precision != PP_PREC_FP64 && cfg->precision != PP_PREC_MIXED) ||
       (cfg->precision == PP_PREC_MIXED && (cfg->inner_maxit < 1 || cfg->inner_maxit > 60)) ||
       cfg->checkpoint_stride < 0 || cfg->nk_fixed_point_pre < 0)

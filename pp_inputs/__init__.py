@@ -18,6 +18,7 @@ which is not published):
 """
 from .mesh import ogrid, box, Mesh  # noqa: F401
 from .workloads import (  # noqa: F401
-    CONFIGS, KIN_HEAVE_PITCH, KIN_FOURIER6, config_mesh, config_mu,
-    fourier6_samples, state_perturbation, free_stream_state, MU_C0, MU_F6_BASE, MU_F6_SCALE, PHYS,
+    CONFIGS, KIN_HEAVE_PITCH, KIN_FOURIER6, KIN_SPLINE8, config_mesh, config_mu,
+    fourier6_samples, state_perturbation, free_stream_state, MU_C0, MU_F6_BASE, MU_F6_SCALE, MU_SPLINE8,
+    PHYS,
 )

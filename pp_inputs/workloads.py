@@ -12,6 +12,8 @@ Motion parametrizations (the kinematics mode is part of the C-ABI config):
   theta = theta0 sin(w t + phi)  (single Fourier mode, Eq. nominal form).
 * ``KIN_FOURIER6``:   mu = (a1, b1, a2, alpha1, beta1, alpha2);
   h = a1 sin wt + b1 cos wt + a2 sin 2wt, theta likewise; w = 2 pi / T.
+* ``KIN_SPLINE8``:    mu = (h0, h1, h2, h3, theta0, theta1, theta2, theta3), the knot values at
+  t = 0, T/8, T/4, 3T/8 of the mirrored periodic cubic splines of Sec. 6.2 (Eq. mirror).
 """
 import numpy as np
 
@@ -19,6 +21,7 @@ from .mesh import ogrid
 
 KIN_HEAVE_PITCH = 0
 KIN_FOURIER6 = 1
+KIN_SPLINE8 = 2
 
 DEG = np.pi / 180.0
 
@@ -37,6 +40,10 @@ MU_C0 = np.array([0.1, 5.0 * DEG, 90.0 * DEG])
 # config-0 motion written in the 6-coefficient form: h = 0.1 sin wt, theta = 5deg cos wt
 MU_F6_BASE = np.array([0.1, 0.0, 0.0, 0.0, 5.0 * DEG, 0.0])
 MU_F6_SCALE = np.array([0.1, 0.1, 0.1, 5.0 * DEG, 5.0 * DEG, 5.0 * DEG])
+# the same motion sampled at the spline knots t = 0, T/8, T/4, 3T/8 (h = 0.1 sin wt,
+# theta = 5deg cos wt)
+_R2 = np.sqrt(0.5)
+MU_SPLINE8 = np.array([0.0, 0.1 * _R2, 0.1, 0.1 * _R2, 5.0 * DEG, 5.0 * DEG * _R2, 0.0, -5.0 * DEG * _R2])
 
 
 def config_mesh(name):
