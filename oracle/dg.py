@@ -187,6 +187,8 @@ def mirrored_knots(half):
 class DG:
     """The semi-discretization on a given mesh; see module docstring."""
 
+    NV = 4   # conservative variables (rho, rho u, rho v, rho E)
+
     def __init__(self, mesh, p, gamma=1.4, Pr=0.72, Mach=0.2, Re=1000.0, kin=KIN_HEAVE_PITCH, T=5.0,
                  farfield=None):
         """farfield: optional boundary state U_b(X) [..., 2] -> [..., 4] of the far-field faces
@@ -200,16 +202,16 @@ class DG:
         self.T = T
         self.omega = 2.0 * np.pi / T
         self.x0 = np.array([1.0 / 3.0, 0.0])
-        pinf = 1.0 / (gamma * Mach * Mach)
-        self.Uinf = np.array([1.0, 1.0, 0.0, pinf / (gamma - 1.0) + 0.5])
+        self.nv = self.NV
+        self.Uinf = self.free_stream()
 
         self.basis = refelem.Basis(p)
         Np = self.Np = self.basis.np
-        self.nb = 4 * Np
+        self.nb = self.nv * Np
         tris = mesh.tris.astype(np.int64)
         V = mesh.verts
         Ne = self.Ne = tris.shape[0]
-        self.Nu = Ne * 4 * Np
+        self.Nu = Ne * self.nv * Np
 
         # connectivity: local face f = edge (v_f, v_{f+1})
         edge = {}
@@ -301,6 +303,32 @@ class DG:
         self.lift_fN = self.lift_f[np.where(self.nbr >= 0, self.nbr_face, 0)][:, :, ::-1, ::-1].copy()
         self.c11 = np.where(self.nbr < 0, C11_ETA * self.mu_visc * self.L / self.detB[:, None], 0.0)
 
+    # ------------------------------------------------------------------ physics (Sec. 6)
+    def free_stream(self):
+        """Free-stream state: density 1, velocity (1, 0), Mach number Mach."""
+        pinf = 1.0 / (self.gam * self.Mach * self.Mach)
+        return np.array([1.0, 1.0, 0.0, pinf / (self.gam - 1.0) + 0.5])
+
+    def flux_inv(self, U):
+        return inviscid_flux(U, self.gam)
+
+    def flux_vis(self, U, dU, adiabatic=False):
+        return viscous_flux(U, dU, self.mu_visc, self.Pr, self.gam, adiabatic)
+
+    def flux_normal(self, U, n, vn):
+        return normal_flux(U, n, vn, self.gam)
+
+    def flux_roe(self, UL, UR, n, vn):
+        return roe_flux(UL, UR, n, vn, self.gam)
+
+    def wall_state(self, Um, vG):
+        """No-slip wall state: interior density and internal energy, wall velocity."""
+        rho = Um[..., 0]
+        e_int = Um[..., 3] / rho - 0.5 * (Um[..., 1] ** 2 + Um[..., 2] ** 2) / rho**2
+        vGb = vG + 0.0 * rho[..., None]
+        return np.stack([rho, rho * vGb[..., 0], rho * vGb[..., 1],
+                         rho * (e_int + 0.5 * (vGb[..., 0] ** 2 + vGb[..., 1] ** 2))], -1)
+
     # ------------------------------------------------------------------ kinematics
     def motion(self, mu, t):
         """(theta, theta', h') of the prescribed motion at time t (Eq. nominal form)."""
@@ -354,12 +382,7 @@ class DG:
         n = np.einsum("dk,ek->ed", Q, self.N[:, f])[:, None, :]        # [Ne, 1, 2]
         vG = self.mesh_velocity(self.Xq_f[:, f], Qd, hd)                 # [Ne, nqf, 2]
         vn = vG[..., 0] * n[..., 0] + vG[..., 1] * n[..., 1]
-        # no-slip wall state: interior density and internal energy, wall velocity
-        rho = Um[..., 0]
-        e_int = Um[..., 3] / rho - 0.5 * (Um[..., 1] ** 2 + Um[..., 2] ** 2) / rho**2
-        vGb = vG + 0.0 * rho[..., None]
-        Ub = np.stack([rho, rho * vGb[..., 0], rho * vGb[..., 1],
-                       rho * (e_int + 0.5 * (vGb[..., 0] ** 2 + vGb[..., 1] ** 2))], -1)
+        Ub = self.wall_state(Um, vG)
         if self.farfield is None:
             Uf = np.broadcast_to(self.Uinf, Um.shape) + 0.0 * Um
         else:
@@ -370,8 +393,6 @@ class DG:
 
     def _face_flux(self, uS, uN, f, Q, Qd, hd, P):
         """Numerical flux H (outward, per unit length) at the quadrature points of local face f."""
-        g = self.gam
-        mu, Pr = self.mu_visc, self.Pr
         Um, dUm, Up, dUp, n, vG, vn, Ub, Uf, Uhat = self._traces(uS, uN, f, Q, Qd, hd, P)
         nf = n[:, 0, :]                                                  # [Ne, 2]
         # lifted gradient of the side that supplies the viscous flux (this face's lifting only)
@@ -383,13 +404,13 @@ class DG:
         tag = self.tag[:, f][:, None, None]
         US = np.where(side, np.where(tag == 1, Ub, Um), Up)
         QS = np.where(side[..., None], Q_own, Q_nbr)
-        FvS_int = viscous_flux(US, QS, mu, Pr, g)
-        FvS_wall = viscous_flux(US, QS, mu, Pr, g, adiabatic=True)
+        FvS_int = self.flux_vis(US, QS)
+        FvS_wall = self.flux_vis(US, QS, adiabatic=True)
         FvS = np.where(tag[..., None] == 1, FvS_wall, FvS_int)
         pen = self.c11[:, f][:, None, None] * (Uhat - Um)
-        inv_int = roe_flux(Um, Up, n, vn, g)
-        inv_far = roe_flux(Um, Uf, n, vn, g)
-        inv_wall = normal_flux(Ub, n, vn, g)
+        inv_int = self.flux_roe(Um, Up, n, vn)
+        inv_far = self.flux_roe(Um, Uf, n, vn)
+        inv_wall = self.flux_normal(Ub, n, vn)
         Hinv = np.where(tag == 0, inv_int, np.where(tag == 1, inv_wall, inv_far))
         H = Hinv - (dot_n(FvS, n) + pen)
         return H, vG
@@ -410,14 +431,12 @@ class DG:
         its t = 0 pose with the mesh at rest (the steady-state problem)."""
         Q, Qd, hd = self.frame(mu, t)
         P = np.einsum("dk,ekl->edl", Q, self.BinvT)                      # grad_x = P grad_xi
-        g = self.gam
         # volume term: int grad_x phi_i . (F_inv - U v_G - F_vis) dX
         U = np.einsum("...eai,qi->...eqa", uS, self.phi_v)
         gphys = np.einsum("edk,qik->eqid", P, self.dphi_v)
         dU = np.einsum("...eai,eqid->...eqad", uS, gphys) + self._volume_lifting(uS, uN, Q, Qd, hd, P)
         vG = self.mesh_velocity(self.Xq_v, Qd, hd)
-        Ftot = inviscid_flux(U, g) - U[..., None] * vG[..., None, :] \
-            - viscous_flux(U, dU, self.mu_visc, self.Pr, g)
+        Ftot = self.flux_inv(U) - U[..., None] * vG[..., None, :] - self.flux_vis(U, dU)
         wq = self.w_v[None, :] * self.detB[:, None]
         r = np.einsum("eq,eqid,...eqad->...eai", wq, gphys, Ftot)
         # face terms: - int_f phi_i H dS
@@ -436,23 +455,24 @@ class DG:
                      "s_own", "s_nbr", "lift_fN", "c11", "tag", "nbr", "nbr_face", "nbr_safe", "BinvT_nbr"):
             setattr(sub, name, getattr(self, name)[elems])
         sub.Ne = len(elems)
-        sub.Nu = sub.Ne * 4 * self.Np
+        sub.Nu = sub.Ne * self.nv * self.Np
         return sub
 
     def jac_blocks_subset(self, u, mu, t, elems):
         """Block rows of the element Jacobian for the given elements only."""
         sub = self.subset(elems)
         nb, Np = self.nb, self.Np
-        us = np.asarray(u, dtype=np.float64).reshape(self.Ne, 4, Np)
+        nv = self.nv
+        us = np.asarray(u, dtype=np.float64).reshape(self.Ne, nv, Np)
         uS = us[np.asarray(elems)]
         uN = us[sub.nbr_safe]
-        E = np.eye(nb).reshape(nb, 1, 4, Np)
+        E = np.eye(nb).reshape(nb, 1, nv, Np)
         n = sub.Ne
         out = np.zeros((n, 4, nb, nb))
         rS = sub.residual_local(uS[None] + 1j * CS_STEP * E, uN[None] + 0j, mu, t)
         out[:, 0] = np.transpose(np.imag(rS).reshape(nb, n, nb), (1, 2, 0)) / CS_STEP
         for f in range(3):
-            dN = np.zeros((nb, 1, 3, 4, Np))
+            dN = np.zeros((nb, 1, 3, nv, Np))
             dN[:, :, f] = E
             rN = sub.residual_local(uS[None] + 0j, uN[None] + 1j * CS_STEP * dN, mu, t)
             blk = np.transpose(np.imag(rN).reshape(nb, n, nb), (1, 2, 0)) / CS_STEP
@@ -462,21 +482,21 @@ class DG:
 
     def residual_subset(self, u, mu, t, elems):
         sub = self.subset(elems)
-        us = np.asarray(u, dtype=np.float64).reshape(self.Ne, 4, self.Np)
+        us = np.asarray(u, dtype=np.float64).reshape(self.Ne, self.nv, self.Np)
         return sub.residual_local(us[np.asarray(elems)], us[sub.nbr_safe], mu, t)
 
     def gather(self, u):
-        u = u.reshape(u.shape[:-1] + (self.Ne, 4, self.Np)) if u.shape[-1] == self.Nu else u
+        u = u.reshape(u.shape[:-1] + (self.Ne, self.nv, self.Np)) if u.shape[-1] == self.Nu else u
         return u[..., self.nbr_safe, :, :]
 
     def residual(self, u, mu, t):
-        us = np.asarray(u).reshape(np.shape(u)[:-1] + (self.Ne, 4, self.Np))
+        us = np.asarray(u).reshape(np.shape(u)[:-1] + (self.Ne, self.nv, self.Np))
         return self.residual_local(us, us[..., self.nbr_safe, :, :], mu, t).reshape(np.shape(u))
 
     # ------------------------------------------------------------------ QoI (Eq. qoi)
     def qoi_rate(self, u, mu, t):
         """Instantaneous power P^h and x-force F_x^h the fluid exerts on the airfoil."""
-        us = np.asarray(u).reshape(np.shape(u)[:-1] + (self.Ne, 4, self.Np))
+        us = np.asarray(u).reshape(np.shape(u)[:-1] + (self.Ne, self.nv, self.Np))
         uN = us[..., self.nbr_safe, :, :]
         Q, Qd, hd = self.frame(mu, t)
         P = np.einsum("dk,ekl->edl", Q, self.BinvT)
@@ -495,14 +515,15 @@ class DG:
     def jac_blocks(self, u, mu, t):
         """Element block Jacobian by complex step: [Ne, 4 slots, nb, nb] (rows (a,i), cols (b,j))."""
         nb, Ne, Np = self.nb, self.Ne, self.Np
-        us = np.asarray(u, dtype=np.float64).reshape(Ne, 4, Np)
+        nv = self.nv
+        us = np.asarray(u, dtype=np.float64).reshape(Ne, nv, Np)
         uN = us[self.nbr_safe]
-        E = np.eye(nb).reshape(nb, 1, 4, Np)
+        E = np.eye(nb).reshape(nb, 1, nv, Np)
         out = np.zeros((Ne, 4, nb, nb))
         rS = self.residual_local(us[None] + 1j * CS_STEP * E, uN[None] + 0j, mu, t)
         out[:, 0] = np.transpose(np.imag(rS).reshape(nb, Ne, nb), (1, 2, 0)) / CS_STEP
         for f in range(3):
-            dN = np.zeros((nb, 1, 3, 4, Np))
+            dN = np.zeros((nb, 1, 3, nv, Np))
             dN[:, :, f] = E
             rN = self.residual_local(us[None] + 0j, uN[None] + 1j * CS_STEP * dN, mu, t)
             blk = np.transpose(np.imag(rN).reshape(nb, Ne, nb), (1, 2, 0)) / CS_STEP
@@ -529,7 +550,7 @@ class DG:
         return self.blocks_to_sparse(self.jac_blocks(u, mu, t))
 
     def mass(self):
-        blocks = [sp.coo_matrix(self.detB[e] * self.Mref) for e in range(self.Ne) for _ in range(4)]
+        blocks = [sp.coo_matrix(self.detB[e] * self.Mref) for e in range(self.Ne) for _ in range(self.nv)]
         return sp.block_diag(blocks, format="csr")
 
     def dr_dmu(self, u, mu, t):
@@ -546,10 +567,10 @@ class DG:
         """d(P^h, F_x^h)/du [2, Nu]: the QoI is face-local to wall elements, so one
         complex perturbation of local dof (a, i) in every element at once is exact."""
         nb, Ne, Np = self.nb, self.Ne, self.Np
-        us = np.asarray(u, dtype=np.float64).reshape(Ne, 4, Np)
+        us = np.asarray(u, dtype=np.float64).reshape(Ne, self.nv, Np)
         Q, Qd, hd = self.frame(mu, t)
         P = np.einsum("dk,ekl->edl", Q, self.BinvT)
-        E = np.eye(nb).reshape(nb, 1, 4, Np)
+        E = np.eye(nb).reshape(nb, 1, self.nv, Np)
         uS = us[None] + 1j * CS_STEP * E
         uN = us[self.nbr_safe][None] + 0j
         out = np.zeros((2, Ne, nb))
