@@ -20,6 +20,11 @@
  *   (i/p, j/p); element vertex k maps to the k-th corner.
  * - Work is issued on the context's stream; calls that return host values
  *   synchronize that stream before returning.
+ * - Each Arnoldi step of the linear solves is one cooperative launch whose CTAs
+ *   wait on one another at grid barriers (one CTA per SM, all resident; the
+ *   barrier words belong to the context).  Two contexts solving at the same time
+ *   on one device compete for the SMs; a barrier wait is bounded (about one
+ *   second), after which the call fails with PP_ECUDA instead of hanging.
  * - Nondimensionalization: chord 1, leading edge at the origin, free stream
  *   rho = 1, velocity (1, 0), p = 1/(gamma Mach^2), viscosity 1/Re.
  */
