@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--profile-step", type=int, default=0, metavar="NT",
                     help="profiler capture mode: one primal + adjoint sweep over NT steps of the workload's "
                          "step size (period and motion amplitudes scaled by NT / Nt), no timing, no bench line")
+    ap.add_argument("--compare-precisions", action="store_true",
+                    help="one primal period + adjoint sweep of --config from the free stream in FP64 and in "
+                         "mixed precision; prints wall times and the mixed arm's relative differences, no bench line")
+    ap.add_argument("--gmres-maxit", type=int, default=0, help="GMRES cap per linear solve (0: the library default)")
     return ap.parse_args()
 
 
@@ -380,6 +384,53 @@ def roofline_for(kernel, res, peaks, fp64_tflops, c, sustained):
                     "L2-resident" % (ne * 3 * nb * nb * word / 1e6)}
 
 
+def compare_precisions(args):
+    """One period of --config (primal sweep, then the adjoint sweep with F = J_E, dF/dmu) from
+    the free stream, once in FP64 and once with PP_PREC_MIXED; prints one JSON line with the
+    wall times around the public calls and the mixed arm's relative differences in u^(Nt),
+    lambda^(0), the QoI rates and dF/dmu."""
+    import numpy as np
+    import torch
+
+    from paper_1512_00616_gb300 import api as A
+    from pp_inputs import CONFIGS, PHYS, config_mesh, config_mu, free_stream_state
+
+    c = CONFIGS[args.config]
+    mesh = config_mesh(args.config)
+    mu = config_mu(args.config)
+    T = PHYS["T"]
+    res = {}
+    for name, prec in (("fp64", A.PP_PREC_FP64), ("mixed", A.PP_PREC_MIXED)):
+        over = dict(gmres_maxit=args.gmres_maxit) if args.gmres_maxit > 0 else {}
+        ctx = A.pp_create(A.pp_config_default(p=c["p"], kin=c["kin"], T=T, precision=prec, **over))
+        m = A.pp_mesh_create(ctx, mesh.verts, mesh.tris, mesh.ftag)
+        ne, _, nu = A.pp_mesh_info(m)
+        u0 = torch.tensor(free_stream_state(ne, c["p"]).reshape(-1), dtype=torch.float64, device="cuda")
+        uN, lamN, lam0 = torch.zeros_like(u0), torch.zeros_like(u0), torch.zeros_like(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q = A.pp_primal_period(ctx, m, mu, u0, c["Nt"], u_final=uN)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        g = A.pp_adjoint_sweep(ctx, lamN, lam0, weights=np.array([-1.0 / T, 0.0]), n_mu=len(mu))
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res[name] = dict(uN=uN.cpu().numpy(), lam0=lam0.cpu().numpy(), q=np.asarray(q), g=np.asarray(g),
+                         times=[t1 - t0, t2 - t1], counts=A.pp_sweep_counts(ctx), nu=int(nu))
+        A.pp_mesh_destroy(m)
+        A.pp_destroy(ctx)
+    a, b = res["fp64"], res["mixed"]
+
+    def rel(x, y):
+        return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+    print(json.dumps(dict(config=args.config, dof=a["nu"], Nt=c["Nt"], p=c["p"],
+                          u_Nt_rel=rel(b["uN"], a["uN"]), lam0_rel=rel(b["lam0"], a["lam0"]),
+                          qoi_rel=float(np.max(np.abs(b["q"] - a["q"]) / np.maximum(np.abs(a["q"]), 1e-300))),
+                          grad_rel=rel(b["g"], a["g"]), fp64_s=a["times"], mixed_s=b["times"],
+                          counts_fp64=str(a["counts"]), counts_mixed=str(b["counts"]))))
+
+
 def profile_step(args):
     """One primal sweep plus one adjoint sweep (F = J_E, dF/dmu) over args.profile_step steps
     of the workload's step size, from the free stream, for profiler captures.  A shorter
@@ -423,6 +474,9 @@ def main():
         return
     if args.profile_step > 0:
         profile_step(args)
+        return
+    if args.compare_precisions:
+        compare_precisions(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
